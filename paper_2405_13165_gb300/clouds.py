@@ -1,0 +1,369 @@
+"""Seeded synthetic particle clouds shaped like the paper's workloads.
+
+This module only *produces inputs*: lattice positions with jitter, particle
+types, normals, smoothing lengths, masses and smooth test fields.  It holds none
+of the method's arithmetic (no neighbour search, PCA, stencils or remap), so
+both the CUDA path and the CPU oracle may consume what it generates.
+
+Shapes (all lengths in metres, h = 3.5 dx everywhere, jitter +-0.1 dx):
+
+* ``cube_on_sheet``  -- a 3D cube resting on a one-layer film sheet, the
+  cube's footprint removed from the sheet (Sec. 7.1 / 7.3 style geometry).
+* ``jet_on_plate``   -- a vertical 3D cylinder standing on a plate, feeding a
+  radial one-layer film disc (the cleaning-jet shape of Sec. 7.3).
+* ``shallow_layer``  -- a shallow 3D layer in a box or cylinder, thin compared
+  with h (the steady shallow-cylinder experiment of Sec. 7.1).
+
+Particle types follow Sec. 2.3: 3D particles touching the plate are WALL, 3D
+particles on exposed faces are FREE_SURFACE, the rest INTERIOR; film (2D)
+particles are all WALL (Sec. 4.2).  Wall and film particles are jittered in
+plane only, so they lie exactly on the plate.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SEED_BASE = 2405_13165
+
+MODEL_3D = 0
+MODEL_2D = 1
+TYPE_INTERIOR = 0
+TYPE_FREE_SURFACE = 1
+TYPE_WALL = 2
+
+USER_TO_2D = 1  # bit set by a user-defined criterion requesting 3D -> 2D
+USER_TO_3D = 2  # bit set by a user-defined criterion requesting 2D -> 3D
+
+RHO_WATER = 1000.0   # Sec. 7.1
+ETA_WATER = 1.0e-3   # Sec. 7.1
+
+
+@dataclasses.dataclass
+class Cloud:
+    """Structure-of-arrays particle state (caller order)."""
+    pos_h: np.ndarray    # float32 [N,4]  x, y, z, h
+    model: np.ndarray    # uint8  [N]     MODEL_3D / MODEL_2D
+    ptype: np.ndarray    # uint8  [N]     TYPE_*
+    normal: np.ndarray   # float32 [N,4]  inward unit wall normal (0 if none)
+    vp: np.ndarray       # float32 [N,4]  u, v, w, p  (velocity + pressure)
+    rho: np.ndarray      # float32 [N]
+    eta: np.ndarray      # float32 [N]
+    mass: np.ndarray     # float32 [N]
+    diam: np.ndarray     # float32 [N]    droplet diameter, V = pi d^3 / 6
+    hfilm: np.ndarray    # float32 [N]    film height (2D particles)
+    h3d: np.ndarray      # float32 [N]    user-prescribed 3D resolution
+    user: np.ndarray     # uint8  [N]     USER_* bits
+    last: np.ndarray     # uint8  [N]     1 if transitioned in previous step
+    dx: float = 0.0
+    name: str = ""
+
+    @property
+    def n(self) -> int:
+        return int(self.pos_h.shape[0])
+
+    @property
+    def vol(self) -> np.ndarray:
+        """Particle volume V = m / rho (= pi d^3 / 6 for droplets)."""
+        return (self.mass.astype(np.float64) / self.rho.astype(np.float64)).astype(np.float32)
+
+    @property
+    def fields(self) -> np.ndarray:
+        return self.vp
+
+    def take(self, idx: np.ndarray) -> "Cloud":
+        kw = {}
+        for f in dataclasses.fields(self):
+            v = getattr(self, f.name)
+            kw[f.name] = np.ascontiguousarray(v[idx]) if isinstance(v, np.ndarray) else v
+        return Cloud(**kw)
+
+    def arrays(self) -> dict:
+        return {f.name: getattr(self, f.name) for f in dataclasses.fields(self)
+                if isinstance(getattr(self, f.name), np.ndarray)}
+
+
+def concat(clouds: list[Cloud], name: str = "") -> Cloud:
+    kw = {}
+    for f in dataclasses.fields(Cloud):
+        vals = [getattr(c, f.name) for c in clouds]
+        if isinstance(vals[0], np.ndarray):
+            kw[f.name] = np.ascontiguousarray(np.concatenate(vals, axis=0))
+        else:
+            kw[f.name] = vals[0]
+    kw["name"] = name
+    return Cloud(**kw)
+
+
+def sinusoid_fields(xyz: np.ndarray, rng: np.random.Generator, modes: int = 4,
+                    kmin: float = 1.0, kmax: float = 8.0) -> np.ndarray:
+    """u, v, w, p = sum of `modes` sinusoids sin(kappa . x + phi).
+
+    kappa has a direction uniform on the sphere and |kappa| ~ U[kmin, kmax]
+    (rad/m); phi ~ U[0, 2 pi).  Returns float32 [N,4].
+    """
+    out = np.zeros((xyz.shape[0], 4), dtype=np.float64)
+    for f in range(4):
+        for _ in range(modes):
+            d = rng.normal(size=3)
+            d /= np.linalg.norm(d)
+            k = d * rng.uniform(kmin, kmax)
+            phi = rng.uniform(0.0, 2.0 * math.pi)
+            out[:, f] += np.sin(xyz @ k + phi)
+    return out.astype(np.float32)
+
+
+def _finish(xyz: np.ndarray, model: np.ndarray, ptype: np.ndarray, normal: np.ndarray,
+            film_h: float, dx: float, rng: np.random.Generator, name: str) -> Cloud:
+    n = xyz.shape[0]
+    h = 3.5 * dx
+    pos_h = np.empty((n, 4), dtype=np.float32)
+    pos_h[:, :3] = xyz.astype(np.float32)
+    pos_h[:, 3] = np.float32(h)
+    rho = np.full(n, RHO_WATER, dtype=np.float32)
+    eta = np.full(n, ETA_WATER, dtype=np.float32)
+    vol = np.where(model == MODEL_3D, dx ** 3, dx * dx * film_h)
+    mass = (RHO_WATER * vol).astype(np.float32)
+    diam = np.cbrt(6.0 * vol / math.pi).astype(np.float32)
+    hfilm = np.where(model == MODEL_2D, film_h, 0.0).astype(np.float32)
+    vp = sinusoid_fields(pos_h[:, :3].astype(np.float64), rng)
+    return Cloud(pos_h=pos_h, model=model.astype(np.uint8), ptype=ptype.astype(np.uint8),
+                 normal=normal.astype(np.float32), vp=vp, rho=rho, eta=eta, mass=mass,
+                 diam=diam, hfilm=hfilm, h3d=np.full(n, h, dtype=np.float32),
+                 user=np.zeros(n, np.uint8), last=np.zeros(n, np.uint8), dx=dx, name=name)
+
+
+def _jitter(xyz: np.ndarray, planar: np.ndarray, dx: float, rng: np.random.Generator) -> np.ndarray:
+    j = rng.uniform(-0.1 * dx, 0.1 * dx, size=xyz.shape)
+    j[planar, 2] = 0.0
+    return xyz + j
+
+
+def cube_on_sheet(dx: float = 0.02, cube: float = 0.3, sheet: float = 1.0,
+                  film_h_factor: float = 0.3, seed: int = SEED_BASE + 1) -> Cloud:
+    """3D cube (edge `cube`) resting on a one-layer film sheet (edge `sheet`).
+
+    The cube is centred on the sheet; its bottom layer (z = 0) is 3D WALL with
+    normal +z, its side and top layers FREE_SURFACE, the rest INTERIOR.  Film
+    particles share the cube's lattice in x/y; those under the cube's footprint
+    are removed.
+    """
+    rng = np.random.default_rng(seed)
+    m = int(round(cube / dx))
+    s = int(round(sheet / dx))
+    off = (s - m) // 2
+    # cube lattice indices (i, j, k); film lattice indices (i, j)
+    ii, jj, kk = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
+    cx = (off + ii + 0.5) * dx
+    cy = (off + jj + 0.5) * dx
+    cz = kk * dx
+    ctype = np.full(ii.shape, TYPE_INTERIOR, np.uint8)
+    face = (ii == 0) | (ii == m - 1) | (jj == 0) | (jj == m - 1) | (kk == m - 1)
+    ctype[face] = TYPE_FREE_SURFACE
+    ctype[kk == 0] = TYPE_WALL
+    fi, fj = np.meshgrid(np.arange(s), np.arange(s), indexing="ij")
+    fi, fj = fi.ravel(), fj.ravel()
+    keep = ~((fi >= off) & (fi < off + m) & (fj >= off) & (fj < off + m))
+    fi, fj = fi[keep], fj[keep]
+    fx = (fi + 0.5) * dx
+    fy = (fj + 0.5) * dx
+    xyz = np.concatenate([np.stack([cx, cy, cz], 1), np.stack([fx, fy, np.zeros_like(fx)], 1)])
+    model = np.concatenate([np.full(cx.shape, MODEL_3D), np.full(fx.shape, MODEL_2D)]).astype(np.uint8)
+    ptype = np.concatenate([ctype, np.full(fx.shape, TYPE_WALL, np.uint8)])
+    planar = ptype == TYPE_WALL
+    normal = np.zeros((xyz.shape[0], 4), np.float32)
+    normal[planar, 2] = 1.0
+    xyz = _jitter(xyz, planar, dx, rng)
+    return _finish(xyz, model, ptype, normal, film_h_factor * dx, dx, rng,
+                   f"cube_on_sheet(dx={dx:g})")
+
+
+def _jet_lattice(dx: float, r_cyl: float, height: float, r_film: float, plate: float):
+    c = 0.5 * plate
+    nr = int(math.floor(r_cyl / dx))
+    ii, jj = np.meshgrid(np.arange(-nr, nr + 1), np.arange(-nr, nr + 1), indexing="ij")
+    rr = np.hypot(ii * dx, jj * dx)
+    inside = rr <= r_cyl
+    ring = inside & (rr > r_cyl - dx)
+    nk = int(math.floor(height / dx)) + 1
+    nf = int(math.floor(r_film / dx))
+    fi, fj = np.meshgrid(np.arange(-nf, nf + 1), np.arange(-nf, nf + 1), indexing="ij")
+    fr = np.hypot(fi * dx, fj * dx)
+    film = (fr <= r_film) & (fr > r_cyl)
+    return c, ii[inside], jj[inside], ring[inside], nk, fi[film], fj[film]
+
+
+def jet_on_plate_count(dx: float, r_cyl: float = 0.05, height: float = 0.5,
+                       r_film: float = 1.0, plate: float = 2.0) -> int:
+    _, ci, _, _, nk, fi, _ = _jet_lattice(dx, r_cyl, height, r_film, plate)
+    return int(ci.size * nk + fi.size)
+
+
+def jet_on_plate(dx: float | None = 0.004, n_target: int | None = None, r_cyl: float = 0.05,
+                 height: float = 0.5, r_film: float = 1.0, plate: float = 2.0,
+                 film_h_factor: float = 0.3, seed: int = SEED_BASE + 2) -> Cloud:
+    """Vertical 3D cylinder (radius r_cyl, height) on a plate, radial film disc.
+
+    If `n_target` is given, dx is bisected (shape ratios kept) until the
+    particle count is within 1 % of it.
+    """
+    if n_target is not None:
+        lo, hi = 1e-4, 0.05
+        for _ in range(60):
+            mid = math.sqrt(lo * hi)
+            cnt = jet_on_plate_count(mid, r_cyl, height, r_film, plate)
+            if abs(cnt - n_target) <= 0.01 * n_target:
+                break
+            if cnt > n_target:
+                lo = mid
+            else:
+                hi = mid
+        dx = mid
+    rng = np.random.default_rng(seed)
+    c, ci, cj, ring, nk, fi, fj = _jet_lattice(dx, r_cyl, height, r_film, plate)
+    kk = np.repeat(np.arange(nk)[None, :], ci.size, 0).ravel()
+    cii = np.repeat(ci, nk)
+    cjj = np.repeat(cj, nk)
+    rng_ring = np.repeat(ring, nk)
+    cx = c + cii * dx
+    cy = c + cjj * dx
+    cz = kk * dx
+    ctype = np.full(cx.shape, TYPE_INTERIOR, np.uint8)
+    ctype[rng_ring | (kk == nk - 1)] = TYPE_FREE_SURFACE
+    ctype[kk == 0] = TYPE_WALL
+    fx = c + fi * dx
+    fy = c + fj * dx
+    xyz = np.concatenate([np.stack([cx, cy, cz], 1), np.stack([fx, fy, np.zeros_like(fx)], 1)])
+    model = np.concatenate([np.full(cx.shape, MODEL_3D), np.full(fx.shape, MODEL_2D)]).astype(np.uint8)
+    ptype = np.concatenate([ctype, np.full(fx.shape, TYPE_WALL, np.uint8)])
+    planar = ptype == TYPE_WALL
+    normal = np.zeros((xyz.shape[0], 4), np.float32)
+    normal[planar, 2] = 1.0
+    xyz = _jitter(xyz, planar, dx, rng)
+    return _finish(xyz, model, ptype, normal, film_h_factor * dx, dx, rng,
+                   f"jet_on_plate(dx={dx:.6g})")
+
+
+def shallow_layer(dx: float, depth_layers: int, extent: float, cylinder: bool = True,
+                  h_factor: float = 3.5, seed: int = SEED_BASE + 7, jitter: bool = True) -> Cloud:
+    """Shallow 3D layer standing on a floor, in a cylinder (or square box).
+
+    Floor layer: WALL, normal +z.  Side-wall ring (cylinder) or side faces
+    (box): WALL with a horizontal inward normal.  Top layer: FREE_SURFACE.
+    Everything else INTERIOR.  Used for the steady shallow-cylinder checks of
+    Sec. 7.1 (floor particles transition, side-wall particles do not).
+    """
+    rng = np.random.default_rng(seed)
+    n = int(round(extent / dx))
+    ii, jj = np.meshgrid(np.arange(-n, n + 1), np.arange(-n, n + 1), indexing="ij")
+    x = ii.ravel() * dx
+    y = jj.ravel() * dx
+    if cylinder:
+        r = np.hypot(x, y)
+        keep = r <= extent + 1e-9
+        x, y, r = x[keep], y[keep], r[keep]
+        side = r > extent - dx + 1e-9
+        nrm_xy = -np.stack([x, y], 1) / np.maximum(r, 1e-30)[:, None]
+    else:
+        side = (np.abs(x) > extent - dx / 2) | (np.abs(y) > extent - dx / 2)
+        nrm_xy = np.zeros((x.size, 2))
+        nrm_xy[np.abs(x) > extent - dx / 2, 0] = -np.sign(x[np.abs(x) > extent - dx / 2])
+        nrm_xy[np.abs(y) > extent - dx / 2, 1] = -np.sign(y[np.abs(y) > extent - dx / 2])
+        nn = np.linalg.norm(nrm_xy, axis=1)
+        nrm_xy[nn > 0] /= nn[nn > 0, None]
+    xs, ys, zs, ts, ns = [], [], [], [], []
+    for k in range(depth_layers):
+        t = np.full(x.shape, TYPE_INTERIOR, np.uint8)
+        nr = np.zeros((x.size, 3))
+        if k == depth_layers - 1:
+            t[:] = TYPE_FREE_SURFACE
+        t[side] = TYPE_WALL
+        nr[side, :2] = nrm_xy[side]
+        if k == 0:
+            t[:] = TYPE_WALL
+            nr[~side] = (0.0, 0.0, 1.0)
+            nr[side, :2] = nrm_xy[side]
+        xs.append(x); ys.append(y); zs.append(np.full(x.shape, k * dx)); ts.append(t); ns.append(nr)
+    xyz = np.stack([np.concatenate(xs), np.concatenate(ys), np.concatenate(zs)], 1)
+    ptype = np.concatenate(ts)
+    nrm = np.concatenate(ns)
+    floor = (np.abs(xyz[:, 2]) < 1e-12)
+    if jitter:
+        j = rng.uniform(-0.1 * dx, 0.1 * dx, size=xyz.shape)
+        j[floor, 2] = 0.0
+        xyz = xyz + j
+    normal = np.zeros((xyz.shape[0], 4), np.float32)
+    normal[:, :3] = nrm
+    model = np.full(xyz.shape[0], MODEL_3D, np.uint8)
+    c = _finish(xyz, model, ptype, normal, 0.0, dx, rng, f"shallow_layer(dx={dx:g})")
+    c.pos_h[:, 3] = np.float32(h_factor * dx)
+    c.h3d[:] = np.float32(h_factor * dx)
+    return c
+
+
+def flat_film(dx: float, extent: float, film_h: float, seed: int = SEED_BASE + 8,
+              jitter: bool = True, h_factor: float = 3.5) -> Cloud:
+    """Single layer of 2D film particles on z = 0 over [0, extent]^2."""
+    rng = np.random.default_rng(seed)
+    n = int(round(extent / dx))
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    xyz = np.stack([(ii.ravel() + 0.5) * dx, (jj.ravel() + 0.5) * dx, np.zeros(ii.size)], 1)
+    if jitter:
+        j = rng.uniform(-0.1 * dx, 0.1 * dx, size=xyz.shape)
+        j[:, 2] = 0.0
+        xyz = xyz + j
+    model = np.full(xyz.shape[0], MODEL_2D, np.uint8)
+    ptype = np.full(xyz.shape[0], TYPE_WALL, np.uint8)
+    normal = np.zeros((xyz.shape[0], 4), np.float32)
+    normal[:, 2] = 1.0
+    c = _finish(xyz, model, ptype, normal, film_h, dx, rng, f"flat_film(dx={dx:g})")
+    c.pos_h[:, 3] = np.float32(h_factor * dx)
+    c.h3d[:] = np.float32(h_factor * dx)
+    return c
+
+
+def random_cloud(n: int, seed: int, box: float = 1.0, h_lo: float = 0.08, h_hi: float = 0.12,
+                 frac2d: float = 0.3) -> Cloud:
+    """Unstructured cloud with variable h and random models/types (edge cases)."""
+    rng = np.random.default_rng(seed)
+    xyz = rng.uniform(0, box, size=(n, 3))
+    model = (rng.uniform(size=n) < frac2d).astype(np.uint8)
+    xyz[model == MODEL_2D, 2] = 0.0
+    ptype = rng.integers(0, 3, size=n).astype(np.uint8)
+    ptype[model == MODEL_2D] = TYPE_WALL
+    normal = np.zeros((n, 4), np.float32)
+    normal[:, 2] = 1.0
+    c = _finish(xyz, model, ptype, normal, 0.01, box / max(n, 1) ** (1 / 3), rng, f"random({n})")
+    c.pos_h[:, 3] = rng.uniform(h_lo, h_hi, size=n).astype(np.float32)
+    c.h3d[:] = c.pos_h[:, 3]
+    return c
+
+
+def config_small(seed: int = SEED_BASE + 1) -> Cloud:
+    """Cube 0.3^3 at dx = 0.02 on a 1 x 1 film sheet (about 5.65k particles)."""
+    return cube_on_sheet(0.02, seed=seed)
+
+
+def config_jet_1m(seed: int = SEED_BASE + 2) -> Cloud:
+    """Jet-on-plate cloud with dx bisected to 1M particles (within 1 %)."""
+    return jet_on_plate(None, n_target=1_000_000, seed=seed)
+
+
+def config_diff_2m(seed: int = SEED_BASE + 4) -> Cloud:
+    """Cube-on-sheet shape with dx bisected to 2M particles (within 1 %)."""
+    lo, hi = 1e-3, 0.02
+    for _ in range(60):
+        mid = math.sqrt(lo * hi)
+        m = int(round(0.3 / mid))
+        s = int(round(1.0 / mid))
+        cnt = m ** 3 + s * s - m * m
+        if abs(cnt - 2_000_000) <= 20_000:
+            break
+        if cnt > 2_000_000:
+            lo = mid
+        else:
+            hi = mid
+    return cube_on_sheet(mid, seed=seed)
