@@ -1,0 +1,494 @@
+#!/usr/bin/env python
+"""Benchmark of the per-particle operator pipeline on synthetic clouds.
+
+One step = one pass of the whole path over the cloud, through the C ABI:
+build_neighbours -> classify_pca (+ smoothing) -> remap_switched ->
+build_stencils -> apply_ops -> transpose_map -> apply_ops_backward ->
+build_stencils_backward.  Workload: the jet-impingement cloud (vertical 3D
+cylinder r = 0.05 m, h = 0.5 m on a plate with a radial one-layer film disc
+r = 1 m), dx bisected to 1M particles, h = 3.5 dx, jitter +-0.1 dx, stored in
+cell order.  Inputs are resident in HBM when the timed region starts; L2 is
+flushed (256 MB write) before every timed step.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("particles/s for neighbour+PCA+stencil build, apply_ops GB/s; "
+          "FP32-refined vs FP64 at 1e-4")
+UNIT = "particles/s"
+WORKLOAD = "jet-impingement cloud, 1M particles (cylinder r=0.05 m h=0.5 m + film disc r=1 m)"
+
+# Algorithmic work per unit (see the design notes): bytes of the gather-SpMV,
+# flops of the stencil build per same-model neighbour and per particle.
+APPLY_BYTES_NNZ = {4: 20, 8: 36}
+APPLY_BYTES_N = {4: 88, 8: 168}
+ST3_FLOP_NBR, ST3_FLOP_PART = 210.0, 1200.0
+ST2_FLOP_NBR, ST2_FLOP_PART = 90.0, 1000.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mafp", choices=["mafp", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000, help="particle count of the jet cloud")
+    ap.add_argument("--cpu-sample", type=int, default=200_000,
+                    help="particles of the CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows
+                                    if r[3].replace(".", "", 1).isdigit()), default=None)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_oracle_sample(cloud, m: int):
+    """Run the FP64 oracle pipeline on the first m particles (cell order) of
+    the cloud; returns (seconds, threads, description)."""
+    import oracle
+    sub = cloud.take(np.arange(min(m, cloud.n)))
+    t0 = time.perf_counter()
+    rp, col = oracle.neighbours(sub.pos_h)
+    cl = oracle.classify(sub.pos_h, sub.model, sub.ptype, sub.normal, sub.vol, sub.h3d,
+                         sub.user, rp, col)
+    flag = oracle.smooth(sub.model, cl["preflag"], sub.last, rp, col)
+    oracle.remap(oracle.cloud_state(sub), flag, rp, col)
+    coef, status, cond = oracle.stencils(sub.pos_h, sub.model, rp, col)
+    out = oracle.apply(rp, col, coef, sub.vp)
+    oracle.apply_T(rp, col, coef, out)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = (f"first {sub.n} particles (cell order) of the same cloud; oracle neighbours, "
+            f"detection, smoothing, remap, stencils, apply, apply transpose in FP64")
+    return dt, threads, desc, sub.n
+
+
+def gen_cloud(n):
+    from paper_2405_13165_gb300 import clouds as C
+    if n == 1_000_000:
+        c = C.config_jet_1m()
+    else:
+        c = C.jet_on_plate(None, n_target=n)
+    return C.cell_sorted(c)
+
+
+# ----------------------------------------------------------------- GPU bench
+def bench_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2405_13165_gb300 import mafp as M
+    from paper_2405_13165_gb300.pipeline import Pipeline, cloud_to_device
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    cloud = gen_cloud(args.n)
+    n = cloud.n
+    dtype = M.F32_REFINED
+    ctx = M.Context(n)
+    d = cloud_to_device(cloud, dtype, dev)
+    # size the CSR buffers from one neighbour build
+    probe = torch.empty(1, dtype=torch.int32, device=dev)
+    rp = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    ctx.reset_status()
+    M.build_neighbours(ctx, d["pos_h"], rp, probe, None, None, dtype)
+    nnz = int(rp[n].item())
+    ctx.reset_status()
+    cap_nnz = nnz + 1024
+    pipe = Pipeline(ctx, n, cap_nnz, dtype, dev)
+    tloc = torch.empty(cap_nnz, dtype=torch.int16, device=dev)
+    gout = torch.empty(n, 4, 4, dtype=torch.float32, device=dev)
+    gfields = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    gpos = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    cap_out = 2 * n
+    state_in = {k: d[k] for k in ("pos_h", "vp", "normal", "rho", "eta", "mass", "diam",
+                                  "hfilm", "h3d", "model", "last")}
+    state_in["type"] = d["ptype"]
+    state_out = {k: torch.empty((cap_out,) + tuple(v.shape[1:]), dtype=v.dtype, device=dev)
+                 for k, v in state_in.items()}
+    old2new = torch.empty(n, dtype=torch.int32, device=dev)
+    n_out = torch.empty(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    have_bwd = True
+
+    def step(ev=None):
+        nonlocal have_bwd
+        marks = []
+        def mark():
+            if ev is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                marks.append(e)
+        mark()
+        pipe.neighbours(d)
+        mark()
+        pipe.classify(d)
+        mark()
+        M.remap_switched(ctx, n, state_in, pipe.flag[:n], pipe.row_ptr[: n + 1], pipe.col,
+                         state_out, cap_out, old2new, n_out, dtype)
+        mark()
+        pipe.stencils(d)
+        mark()
+        pipe.apply(d)
+        mark()
+        M.transpose_map(ctx, pipe.row_ptr[: n + 1], pipe.col, tloc)
+        gout.copy_(pipe.out[:n])
+        M.apply_ops_backward(ctx, pipe.row_ptr[: n + 1], pipe.col, tloc, pipe.coef, gout,
+                             gfields, dtype)
+        if have_bwd:
+            try:
+                M.build_stencils_backward(ctx, d["pos_h"], d["model"], pipe.frame[:n],
+                                          pipe.row_ptr[: n + 1], pipe.col, d["fields"], gout,
+                                          gpos, dtype)
+            except M.MafpError as e:
+                if e.code != M.ENOTIMPL:
+                    raise
+                have_bwd = False
+        mark()
+        return marks
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    st = ctx.status()
+    if st["code"] != 0:
+        raise RuntimeError(f"device status after warm-up: {st}")
+
+    # ---- timed region
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t_wall0 = time.perf_counter()
+    per_step, stages = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        marks = step(ev=True)
+        stages.append(marks)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    for marks in stages:
+        per_step.append(marks[0].elapsed_time(marks[-1]))
+    names = ["build_neighbours", "classify_pca", "remap_switched", "build_stencils",
+             "apply_ops", "backward"]
+    stage_ms = {nm: statistics.mean(m[k].elapsed_time(m[k + 1]) for m in stages)
+                for k, nm in enumerate(names)}
+    total_ms = sum(per_step)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_step = total_ms / args.steps
+    value = world * n / (ms_step * 1e-3)
+    st = ctx.status()
+
+    # ---- kernel-level timing on one extra step (same stream, CUDA events)
+    ctx.profile(True)
+    step()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches_per_step = sum(v[0] for v in prof.values())
+
+    # algorithmic work of the candidate dominant kernels
+    model = d["model"]
+    rows = torch.repeat_interleave(torch.arange(n, device=dev), pipe.row_ptr[1: n + 1] -
+                                   pipe.row_ptr[:n])
+    col = pipe.col[:nnz].long()
+    same = model[rows] == model[col]
+    nbr3 = int((same & (model[rows] == 0)).sum().item())
+    nbr2 = int((same & (model[rows] == 1)).sum().item())
+    n3 = int((model == 0).sum().item())
+    n2 = n - n3
+    sm_mhz = clocks.get("sm_mhz") or 1920.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s at the sampled clock
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
+
+    def kernel_ms(prefix):
+        hit = [(k, v) for k, v in prof.items() if k.startswith(prefix)]
+        if not hit:
+            return None, 0
+        launches = sum(v[0] for _, v in hit)
+        return sum(v[1] for _, v in hit) / max(launches, 1), launches
+
+    kernels = {}
+    ms, _ = kernel_ms("k_apply<float")
+    if ms:
+        b = APPLY_BYTES_NNZ[4] * nnz + APPLY_BYTES_N[4] * n
+        kernels["apply_ops"] = {"bound": "hbm", "achieved": b / (ms * 1e-3) / 1e9, "peak": hbm_peak,
+                                "unit": "GB/s", "ms": ms, "algorithmic": b,
+                                "peak_src": hbm_src}
+    ms, _ = kernel_ms("k_stencil<float,float,10")
+    if ms:
+        fl = ST3_FLOP_NBR * nbr3 + ST3_FLOP_PART * n3
+        kernels["build_stencils_3d"] = {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12,
+                                        "peak": fp32_peak, "unit": "TFLOP/s", "ms": ms,
+                                        "algorithmic": fl, "peak_src": "FP32 FMA issue rate at sampled clock"}
+    ms, _ = kernel_ms("k_stencil<float,float,6")
+    if ms:
+        fl = ST2_FLOP_NBR * nbr2 + ST2_FLOP_PART * n2
+        kernels["build_stencils_2d"] = {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12,
+                                        "peak": fp32_peak, "unit": "TFLOP/s", "ms": ms,
+                                        "algorithmic": fl, "peak_src": "FP32 FMA issue rate at sampled clock"}
+    ms, _ = kernel_ms("k_nbr<T,true>")
+    if ms:
+        b = 4 * nnz + 16 * n
+        kernels["nbr_fill"] = {"bound": "hbm", "achieved": b / (ms * 1e-3) / 1e9, "peak": hbm_peak,
+                               "unit": "GB/s", "ms": ms, "algorithmic": b, "peak_src": hbm_src}
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    dominant = None
+    for key, pref in (("apply_ops", "k_apply<float"), ("build_stencils_3d", "k_stencil<float,float,10"),
+                      ("build_stencils_2d", "k_stencil<float,float,6"), ("nbr_fill", "k_nbr<T,true>")):
+        if top[0].startswith(pref):
+            dominant = key
+    if dominant is None:
+        dominant = max(kernels, key=lambda k: kernels[k]["ms"]) if kernels else None
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f)
+    except OSError:
+        traffic = {}
+    roof = None
+    if dominant:
+        k = kernels[dominant]
+        roof = {"kernel": dominant, "bound": k["bound"], "achieved": round(k["achieved"], 2),
+                "peak": round(k["peak"], 1), "unit": k["unit"],
+                "frac": round(k["achieved"] / k["peak"], 4),
+                "traffic": traffic.get(dominant), "peak_source": k["peak_src"],
+                "launch_ms": round(k["ms"], 4)}
+
+    # ---- FP64 path on the same cloud (the plain FP64 GPU baseline)
+    fp64 = None
+    if not args.no_fp64:
+        d64 = cloud_to_device(cloud, M.F64, dev)
+        pipe64 = Pipeline(ctx, n, cap_nnz, M.F64, dev)
+        for _ in range(1):
+            pipe64.step(d64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k64 = max(2, min(args.steps, 3))
+        t64 = 0.0
+        for _ in range(k64):
+            flush.fill_(1)
+            e0.record(stream)
+            pipe64.neighbours(d64)
+            pipe64.classify(d64)
+            pipe64.stencils(d64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t64 += e0.elapsed_time(e1)
+        t64 /= k64
+        e0.record(stream)
+        pipe.neighbours(d)
+        pipe.classify(d)
+        pipe.stencils(d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t32 = e0.elapsed_time(e1)
+        fp64 = {"build_ms_fp64": round(t64, 3), "build_ms_fp32_refined": round(t32, 3),
+                "speedup": round(t64 / t32, 2),
+                "build_particles_per_s_fp32_refined": round(n / (t32 * 1e-3), 1),
+                "build_particles_per_s_fp64": round(n / (t64 * 1e-3), 1)}
+        del pipe64, d64
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        keys = ("pos_h", "model", "ptype", "normal", "vol", "h3d", "user", "last", "fields")
+        host = {k: d[k].cpu().pin_memory() for k in keys}
+        out_host = torch.empty((n, 4, 4), dtype=torch.float32).pin_memory()
+        flag_host = torch.empty(n, dtype=torch.uint8).pin_memory()
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = out_host.numel() * 4 + flag_host.numel()
+        dd = {k: torch.empty_like(d[k]) for k in keys}
+        dd["vp"] = dd["fields"]
+        tot = 0.0
+        for it in range(args.steps + 1):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in keys:
+                dd[k].copy_(host[k], non_blocking=True)
+            pipe.step(dd)
+            out_host.copy_(pipe.out[:n], non_blocking=True)
+            flag_host.copy_(pipe.flag[:n], non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it > 0:
+                tot += e0.elapsed_time(e1)
+        e2e_ms = tot / args.steps
+        e2e = {"value": round(world * n / (e2e_ms * 1e-3), 1), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": round(e2e_ms, 3),
+               "path": "pinned host -> device copies, neighbours+detection+stencils+apply, "
+                       "device -> pinned host of derivatives and flags"}
+
+    # ---- CPU baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, thr, desc, m = cpu_oracle_sample(cloud, args.cpu_sample)
+        cpu = {"value": round(m / dt, 1), "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": desc, "seconds": round(dt, 2)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded jet-on-plate cloud)",
+            "config": {"workload": WORKLOAD, "n_particles": n, "nnz": nnz, "n_3d": n3, "n_2d": n2,
+                       "dx": round(cloud.dx, 7), "precision": "FP32 refined, FP64 retakes",
+                       "step": "neighbours, detection, remap, stencils, apply, apply transpose"
+                               + (", stencil adjoint" if have_bwd else ""),
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "build_particles_per_s": round(n / ((stage_ms["build_neighbours"] +
+                                                 stage_ms["classify_pca"] +
+                                                 stage_ms["build_stencils"]) * 1e-3), 1),
+            "apply_ops_gbs": round(kernels.get("apply_ops", {}).get("achieved", 0.0), 1),
+            "roofline": roof,
+            "kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                            for kk, vv in v.items()} for k, v in kernels.items()},
+            "fp64_vs_fp32": fp64,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": int(launches_per_step * args.steps),
+            "device_status": {k: st[k] for k in ("code", "n_fp64_stencil", "n_fp64_eigen",
+                                                 "n_deficient", "n_near", "cells_identity")},
+            "wall_s_timed_region": round(t_wall, 3),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def bench_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cloud = gen_cloud(args.n)
+    m = args.cpu_sample
+    for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
+        pass  # the oracle has no state to warm beyond loading its library
+    import oracle
+    oracle.build()
+    times = []
+    for _ in range(args.steps):
+        dt, thr, desc, mm = cpu_oracle_sample(cloud, m)
+        times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = mm / (ms * 1e-3)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded jet-on-plate cloud)",
+            "config": {"workload": WORKLOAD, "n_particles": cloud.n, "sample_particles": mm},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "kind": "oracle",
+                             "cores": thr, "sample": desc},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

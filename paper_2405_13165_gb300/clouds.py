@@ -367,3 +367,23 @@ def config_diff_2m(seed: int = SEED_BASE + 4) -> Cloud:
         else:
             hi = mid
     return cube_on_sheet(mid, seed=seed)
+
+
+def cell_sorted(cloud: Cloud, cell_factor: float = 1.0 + 1e-6) -> Cloud:
+    """Permute a cloud into cell order: cells of edge max(h) * cell_factor from
+    the bounding-box minimum, keys (cz * ny + cy) * nx + cx, stable in index.
+
+    A Lagrangian code keeps its particles in this order between steps; it is
+    the order the neighbour search's own cell sort produces, so a cloud in it
+    takes the search's sorted path.  Input layout only (no method arithmetic).
+    """
+    P = cloud.pos_h.astype(np.float64)
+    lo = P[:, :3].min(0)
+    hi = P[:, :3].max(0)
+    c = float(P[:, 3].max()) * cell_factor
+    inv_c = 1.0 / c
+    dim = np.floor((hi - lo) / c) + 1.0
+    cc = np.floor((P[:, :3] - lo) * inv_c)
+    cc = np.clip(cc, 0, dim - 1).astype(np.int64)
+    key = (cc[:, 2] * int(dim[1]) + cc[:, 1]) * int(dim[0]) + cc[:, 0]
+    return cloud.take(np.argsort(key, kind="stable"))

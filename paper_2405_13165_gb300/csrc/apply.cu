@@ -1,0 +1,148 @@
+// apply.cu -- stencil application of Eq. GFDM_Definition as a ragged gather-SpMV
+// (four fields x four operators per row) and its transpose through the
+// symmetric-structure map (gather, no atomics).
+#include "internal.cuh"
+
+namespace mafp {
+
+constexpr int kApThreads = 256;
+
+// out[i][f][op] = sum_{e in row i} coef[e].op * fields[col[e]].f
+// A group of G lanes per row; lanes stride over the row with U loads in flight.
+template <typename T, int G, int U>
+__global__ void __launch_bounds__(kApThreads) k_apply(int64_t n, const long long *row_ptr,
+                                                      const int32_t *col,
+                                                      const vec4_t<T> *coef,
+                                                      const vec4_t<T> *fields, T *out) {
+  using V = vec4_t<T>;
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t i = gid; i < n; i += ngroups) {
+    const long long b = row_ptr[i], e1 = row_ptr[i + 1];
+    T acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = T(0);
+    long long e = b + lane;
+    for (; e + (U - 1) * G < e1; e += U * G) {
+      int j[U];
+      V c[U], f[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) j[u] = __ldg(col + e + u * G);
+#pragma unroll
+      for (int u = 0; u < U; ++u) c[u] = ld4(coef + e + u * G);
+#pragma unroll
+      for (int u = 0; u < U; ++u) f[u] = ld4(fields + j[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const T fv[4] = {f[u].x, f[u].y, f[u].z, f[u].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[4 * q + 0] += c[u].x * fv[q];
+          acc[4 * q + 1] += c[u].y * fv[q];
+          acc[4 * q + 2] += c[u].z * fv[q];
+          acc[4 * q + 3] += c[u].w * fv[q];
+        }
+      }
+    }
+    for (; e < e1; e += G) {
+      const int j = __ldg(col + e);
+      const V c = ld4(coef + e);
+      const V f = ld4(fields + j);
+      const T fv[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[4 * q + 0] += c.x * fv[q];
+        acc[4 * q + 1] += c.y * fv[q];
+        acc[4 * q + 2] += c.z * fv[q];
+        acc[4 * q + 3] += c.w * fv[q];
+      }
+    }
+    reduce_scatter<G, 16>(acc);
+    constexpr int PER = 16 / G;
+    T *o = out + 16 * i + lane * PER;
+    if constexpr (PER == 2) {
+      if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float2 *>(o) = make_float2(acc[0], acc[1]);
+      } else {
+        *reinterpret_cast<double2 *>(o) = make_double2(acc[0], acc[1]);
+      }
+    } else if constexpr (PER == 4) {
+      st4(reinterpret_cast<V *>(o), mk4<T>(acc[0], acc[1], acc[2], acc[3]));
+    } else {
+#pragma unroll
+      for (int k = 0; k < PER; ++k) o[k] = acc[k];
+    }
+  }
+}
+
+// gfields[j][f] = sum_{e in row j} sum_op coef[(i, j)].op * gout[i][f][op],
+// i = col[e], (i, j) found at row_ptr[i] + tloc[e].
+template <typename T, int G>
+__global__ void __launch_bounds__(kApThreads) k_apply_T(int64_t n, const long long *row_ptr,
+                                                        const int32_t *col,
+                                                        const uint16_t *tloc,
+                                                        const vec4_t<T> *coef,
+                                                        const vec4_t<T> *gout,
+                                                        vec4_t<T> *gfields) {
+  using V = vec4_t<T>;
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t jr = gid; jr < n; jr += ngroups) {
+    const long long b = row_ptr[jr], e1 = row_ptr[jr + 1];
+    T acc[G < 4 ? 4 : G];
+#pragma unroll
+    for (int k = 0; k < (G < 4 ? 4 : G); ++k) acc[k] = T(0);
+    for (long long e = b + lane; e < e1; e += G) {
+      const int i = __ldg(col + e);
+      const long long ei = row_ptr[i] + tloc[e];
+      const V c = ld4(coef + ei);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const V g = ld4(gout + 4 * (int64_t)i + f);
+        acc[f] += c.x * g.x + c.y * g.y + c.z * g.z + c.w * g.w;
+      }
+    }
+    reduce_scatter<G, (G < 4 ? 4 : G)>(acc);
+    T *o = reinterpret_cast<T *>(gfields + jr);
+    if (lane < 4) o[lane] = acc[0];
+  }
+}
+
+int apply_ops(mafp_ctx *ctx, int64_t n, int32_t dtype, const int64_t *row_ptr, const int32_t *col,
+              const void *coef, const void *fields, void *out, cudaStream_t s) {
+  const long long *rp = reinterpret_cast<const long long *>(row_ptr);
+  const int blocks = grid_for(n * 8, kApThreads, sm_count() * 64);
+  if (dtype == MAFP_F64) {
+    MAFP_TIMED(ctx, s, "k_apply<double,8,2>",
+               k_apply<double, 8, 2><<<blocks, kApThreads, 0, s>>>(n, rp, col, (const double4_16a *)coef,
+                                                        (const double4_16a *)fields, (double *)out));
+  } else {
+    MAFP_TIMED(ctx, s, "k_apply<float,8,4>",
+               k_apply<float, 8, 4><<<blocks, kApThreads, 0, s>>>(n, rp, col, (const float4 *)coef,
+                                                       (const float4 *)fields, (float *)out));
+  }
+  MAFP_LAUNCH_CHECK(ctx);
+  return MAFP_OK;
+}
+
+int apply_ops_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const int64_t *row_ptr,
+                       const int32_t *col, const uint16_t *tloc, const void *coef,
+                       const void *gout, void *gfields, cudaStream_t s) {
+  const long long *rp = reinterpret_cast<const long long *>(row_ptr);
+  const int blocks = grid_for(n * 8, kApThreads, sm_count() * 64);
+  if (dtype == MAFP_F64) {
+    MAFP_TIMED(ctx, s, "k_apply_T<double,8>",
+               k_apply_T<double, 8><<<blocks, kApThreads, 0, s>>>(n, rp, col, tloc, (const double4_16a *)coef,
+                                                       (const double4_16a *)gout, (double4_16a *)gfields));
+  } else {
+    MAFP_TIMED(ctx, s, "k_apply_T<float,8>",
+               k_apply_T<float, 8><<<blocks, kApThreads, 0, s>>>(n, rp, col, tloc, (const float4 *)coef,
+                                                      (const float4 *)gout, (float4 *)gfields));
+  }
+  MAFP_LAUNCH_CHECK(ctx);
+  return MAFP_OK;
+}
+
+}  // namespace mafp

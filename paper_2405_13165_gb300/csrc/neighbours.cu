@@ -1,0 +1,508 @@
+// neighbours.cu -- fixed-radius neighbour search of Eq. Nbd (Sec. 2.2) on a
+// cell list: bounding box -> cell keys -> stable LSD radix sort -> cell ranges
+// -> count (one block per occupied cell, candidate tiles staged in shared
+// memory) -> exclusive scan -> fill -> (row sort when the input order is not
+// the cell order) ; plus the transpose map used by the apply adjoint.
+#include <climits>
+
+#include "internal.cuh"
+
+namespace mafp {
+
+// ---------------------------------------------------------------- grid set-up
+constexpr int kBoxThreads = 256;
+constexpr int kBoxBlocks = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(kBoxThreads) k_bbox(const vec4_t<T> *pos, int64_t n,
+                                                      double *partial) {
+  double v[8] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    vec4_t<T> p = ld4(pos + i);
+    bool ok = isfinite((double)p.x) && isfinite((double)p.y) && isfinite((double)p.z) &&
+              isfinite((double)p.w) && p.w > T(0);
+    if (!ok) {
+      v[7] += 1.0;
+      continue;
+    }
+    v[0] = fmin(v[0], (double)p.x); v[1] = fmin(v[1], (double)p.y); v[2] = fmin(v[2], (double)p.z);
+    v[3] = fmax(v[3], (double)p.x); v[4] = fmax(v[4], (double)p.y); v[5] = fmax(v[5], (double)p.z);
+    v[6] = fmax(v[6], (double)p.w);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = fmin(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+#pragma unroll
+    for (int k = 3; k < 7; ++k) v[k] = fmax(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    v[7] += __shfl_xor_sync(0xffffffffu, v[7], o);
+  }
+  __shared__ double red[kBoxThreads / 32][8];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < 8; ++k) red[w][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    int k = threadIdx.x;
+    double a = red[0][k];
+    for (int ww = 1; ww < kBoxThreads / 32; ++ww)
+      a = k < 3 ? fmin(a, red[ww][k]) : (k < 7 ? fmax(a, red[ww][k]) : a + red[ww][k]);
+    partial[blockIdx.x * 8 + k] = a;
+  }
+}
+
+__global__ void k_grid(const double *partial, int nb, GridDev *g, DevStatus *st,
+                       long long cap_cells) {
+  if (threadIdx.x != 0) return;
+  double v[8] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0, 0.0};
+  for (int b = 0; b < nb; ++b)
+    for (int k = 0; k < 8; ++k) {
+      double a = partial[b * 8 + k];
+      v[k] = k < 3 ? fmin(v[k], a) : (k < 7 ? fmax(v[k], a) : v[k] + a);
+    }
+  g->ok = 0;
+  if (v[7] > 0.0) {
+    st->n_nonfinite += (long long)v[7];
+    set_error(st, MAFP_ENONFINITE, (long long)v[7]);
+    return;
+  }
+  // Strictly larger than every support radius (h_i + h_j)/2 <= max h, so every
+  // member of S_i lies in the 27 cells around i's cell.
+  double c = v[6] * (1.0 + 1e-6);
+  long long ncells = 0;
+  int dim[3];
+  for (int it = 0; it < 64; ++it) {
+    double cells = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      double d = floor((v[3 + a] - v[a]) / c) + 1.0;
+      cells *= d;
+      dim[a] = d < 2e9 ? (int)d : INT_MAX;
+    }
+    if (cells <= (double)cap_cells) {
+      ncells = (long long)dim[0] * dim[1] * dim[2];
+      break;
+    }
+    c *= cbrt(cells / (double)cap_cells) * 1.0001;
+  }
+  if (ncells <= 0) {
+    set_error(st, MAFP_ECAPACITY, cap_cells);
+    return;
+  }
+  for (int a = 0; a < 3; ++a) {
+    g->lo[a] = v[a];
+    g->dim[a] = dim[a];
+  }
+  g->c = c;
+  g->inv_c = 1.0 / c;
+  g->ncells = ncells;
+  g->hmax = v[6];
+  g->ok = 1;
+  st->ncells = ncells;
+  st->cell_size = c;
+  st->not_identity = 0;
+}
+
+template <typename T>
+__global__ void k_hash(const vec4_t<T> *pos, int64_t n, const GridDev *g, uint32_t *keys,
+                       int32_t *vals) {
+  if (!g->ok) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    vec4_t<T> p = ld4(pos + i);
+    double q[3] = {(double)p.x, (double)p.y, (double)p.z};
+    long long c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      long long v = (long long)floor((q[a] - g->lo[a]) * g->inv_c);
+      v = v < 0 ? 0 : (v >= g->dim[a] ? g->dim[a] - 1 : v);
+      c[a] = v;
+    }
+    keys[i] = (uint32_t)((c[2] * g->dim[1] + c[1]) * g->dim[0] + c[0]);
+    vals[i] = (int32_t)i;
+  }
+}
+
+__global__ void k_clear_cells(const GridDev *g, int32_t *cell_start, int32_t *cell_end,
+                              int32_t *n_ucell) {
+  if (!g->ok) return;
+  const long long nc = g->ncells;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_ucell = 0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nc;
+       k += (long long)gridDim.x * blockDim.x) {
+    cell_start[k] = INT_MAX;
+    cell_end[k] = 0;
+  }
+}
+
+// ------------------------------------------------------------- radix sort
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 8;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;
+
+__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const uint32_t *keys, int64_t n,
+                                                              int shift, int32_t *hist,
+                                                              int tiles, const GridDev *g) {
+  if (!g->ok) return;
+  __shared__ int32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  for (int k = threadIdx.x; k < kRadixTile; k += kRadixThreads) {
+    int64_t idx = base + k;
+    if (idx < n) atomicAdd(&cnt[(keys[idx] >> shift) & 255u], 1);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
+    const uint32_t *kin, const int32_t *vin, uint32_t *kout, int32_t *vout, int64_t n, int shift,
+    const long long *offs, int tiles, const GridDev *g) {
+  if (!g->ok) return;
+  __shared__ long long base_d[256];
+  __shared__ int32_t wcnt[kRadixThreads / 32][256];
+  __shared__ int32_t ctot[256];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  base_d[tid] = offs[(int64_t)tid * tiles + blockIdx.x];
+  const unsigned lt = (1u << lane) - 1u;
+  for (int c = 0; c < kRadixItems; ++c) {
+    for (int k = tid; k < (kRadixThreads / 32) * 256; k += kRadixThreads) (&wcnt[0][0])[k] = 0;
+    __syncthreads();
+    const int64_t idx = (int64_t)blockIdx.x * kRadixTile + (int64_t)c * kRadixThreads + tid;
+    const bool valid = idx < n;
+    uint32_t key = valid ? kin[idx] : 0u;
+    int32_t val = valid ? vin[idx] : 0;
+    int d = valid ? (int)((key >> shift) & 255u) : 256;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int rank = __popc(peers & lt);
+    if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    {
+      int run = 0;
+      for (int ww = 0; ww < kRadixThreads / 32; ++ww) {
+        int t = wcnt[ww][tid];
+        wcnt[ww][tid] = run;
+        run += t;
+      }
+      ctot[tid] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      long long p = base_d[d] + wcnt[w][d] + rank;
+      kout[p] = key;
+      vout[p] = val;
+    }
+    __syncthreads();
+    base_d[tid] += ctot[tid];
+    __syncthreads();
+  }
+}
+
+// Exclusive scan of the (digit-major) histogram; reuses the int32->int64 scan.
+// --------------------------------------------------------- cell ranges
+template <typename T>
+__global__ void k_cells(const uint32_t *skeys, const int32_t *svals, int64_t n,
+                        const vec4_t<T> *pos, vec4_t<T> *spos, int32_t *cell_start,
+                        int32_t *cell_end, int32_t *ucell, int32_t *n_ucell, DevStatus *st,
+                        int32_t *order, const GridDev *g) {
+  if (!g->ok) return;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t key = skeys[s];
+    int32_t i = svals[s];
+    st4(spos + s, ld4(pos + i));
+    if (order) order[s] = i;
+    if (i != (int32_t)s) st->not_identity = 1;
+    if (s == 0 || skeys[s - 1] != key) {
+      cell_start[key] = (int32_t)s;
+      int u = atomicAdd(n_ucell, 1);
+      ucell[2 * u] = (int32_t)key;
+      ucell[2 * u + 1] = (int32_t)s;
+    }
+    if (s == n - 1 || skeys[s + 1] != key) cell_end[key] = (int32_t)(s + 1);
+  }
+}
+
+__global__ void k_identity_flag(DevStatus *st) {
+  st->cells_identity = st->not_identity ? 0 : 1;
+}
+
+// --------------------------------------------------------- count / fill
+__device__ __forceinline__ bool in_support64(double xi, double yi, double zi, double hi,
+                                             double xj, double yj, double zj, double hj) {
+  double dx = __dsub_rn(xj, xi), dy = __dsub_rn(yj, yi), dz = __dsub_rn(zj, zi);
+  double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  double r = __dmul_rn(__dadd_rn(hi, hj), 0.5);
+  return d2 <= __dmul_rn(r, r);
+}
+
+// FP32 decision, retaken in FP64 within a 1e-5 relative band of the bound.
+__device__ __forceinline__ bool in_support(const float4 &a, const float4 &b) {
+  float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+  float d2 = (dx * dx + dy * dy) + dz * dz;
+  float r = (a.w + b.w) * 0.5f;
+  float r2 = r * r;
+  float diff = d2 - r2;
+  if (fabsf(diff) <= 1e-5f * r2)
+    return in_support64(a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w);
+  return diff < 0.0f;
+}
+__device__ __forceinline__ bool in_support(const double4_16a &a, const double4_16a &b) {
+  return in_support64(a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w);
+}
+
+constexpr int kNbrThreads = 128;
+constexpr int kNbrSmemBytes = 32768;
+
+template <typename T, bool FILL>
+__global__ void __launch_bounds__(kNbrThreads) k_nbr(
+    const GridDev *g, const int32_t *ucell, const int32_t *n_ucell, const vec4_t<T> *spos,
+    const int32_t *svals, const int32_t *cell_start, const int32_t *cell_end, int32_t *counts,
+    const long long *row_ptr, int32_t *col, long long cap_nnz, int64_t n) {
+  using V = vec4_t<T>;
+  constexpr int CAP = kNbrSmemBytes / sizeof(V);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V *cand = reinterpret_cast<V *>(smem_raw);
+  __shared__ int r_lo[9], r_len[9], r_off[10];
+  if (!g->ok) return;
+  if (FILL && row_ptr[n] > cap_nnz) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = kNbrThreads / 32;
+  const unsigned lt = (1u << lane) - 1u;
+  const int nu = *n_ucell;
+  const int dx_ = g->dim[0], dy_ = g->dim[1], dz_ = g->dim[2];
+  for (int cb = blockIdx.x; cb < nu; cb += gridDim.x) {
+    const int key = ucell[2 * cb], s0 = ucell[2 * cb + 1];
+    const int s1 = cell_end[key];
+    const int cx = key % dx_, cy = (key / dx_) % dy_, cz = key / (dx_ * dy_);
+    if (threadIdx.x < 9) {
+      const int r = threadIdx.x, ddz = r / 3 - 1, ddy = r % 3 - 1;
+      int lo = INT_MAX, hi = 0;
+      if (cz + ddz >= 0 && cz + ddz < dz_ && cy + ddy >= 0 && cy + ddy < dy_) {
+        const int base = key + ddz * dx_ * dy_ + ddy * dx_;
+        const int k0 = cx > 0 ? base - 1 : base, k1 = cx < dx_ - 1 ? base + 1 : base;
+        for (int k = k0; k <= k1; ++k) {
+          lo = min(lo, cell_start[k]);
+          hi = max(hi, cell_end[k]);
+        }
+      }
+      r_lo[r] = lo;
+      r_len[r] = hi > lo ? hi - lo : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int o = 0;
+      for (int r = 0; r < 9; ++r) {
+        r_off[r] = o;
+        o += r_len[r];
+      }
+      r_off[9] = o;
+    }
+    __syncthreads();
+    const bool staged = r_off[9] <= CAP;
+    if (staged) {
+      for (int r = 0; r < 9; ++r)
+        for (int t = threadIdx.x; t < r_len[r]; t += kNbrThreads)
+          cand[r_off[r] + t] = ld4(spos + r_lo[r] + t);
+    }
+    __syncthreads();
+    for (int p = s0 + w; p < s1; p += nw) {
+      const V xi = ld4(spos + p);
+      long long base = 0;
+      if (FILL) base = row_ptr[svals[p]];
+      int cnt = 0;
+      for (int r = 0; r < 9; ++r) {
+        const int len = r_len[r], lo = r_lo[r], off = r_off[r];
+        for (int t0 = 0; t0 < len; t0 += 32) {
+          const int t = t0 + lane;
+          bool hit = false;
+          if (t < len) {
+            const V xj = staged ? cand[off + t] : ld4(spos + lo + t);
+            hit = in_support(xi, xj);
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, hit);
+          if (FILL && hit) col[base + cnt + __popc(m & lt)] = svals[lo + t];
+          cnt += __popc(m);
+        }
+      }
+      if (!FILL && lane == 0) counts[svals[p]] = cnt;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_check_nnz(const long long *row_ptr, int64_t n, long long cap_nnz,
+                            int64_t *nnz_dev, DevStatus *st, const GridDev *g) {
+  if (!g->ok) return;
+  long long nnz = row_ptr[n];
+  st->nnz = nnz;
+  if (nnz_dev) *nnz_dev = nnz;
+  if (nnz > cap_nnz) set_error(st, MAFP_ECAPACITY, nnz);
+}
+
+// Rows come out ascending in cell order; when the input order differs from the
+// cell order each row is sorted (bitonic, one warp per row, in shared memory).
+constexpr int kSortWarps = 4;
+
+__global__ void __launch_bounds__(kSortWarps * 32) k_rowsort(const long long *row_ptr,
+                                                             int32_t *col, int64_t n,
+                                                             long long cap_nnz,
+                                                             DevStatus *st) {
+  if (!st->not_identity) return;
+  if (row_ptr[n] > cap_nnz) return;
+  __shared__ int32_t buf[kSortWarps][kMaxRowSort];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t *a = buf[w];
+  for (int64_t i = (int64_t)blockIdx.x * kSortWarps + w; i < n;
+       i += (int64_t)gridDim.x * kSortWarps) {
+    const long long b = row_ptr[i];
+    const int len = (int)(row_ptr[i + 1] - b);
+    if (len > kMaxRowSort) {
+      if (lane == 0) set_error(st, MAFP_ECAPACITY, len);
+      continue;
+    }
+    int P = 1;
+    while (P < len) P <<= 1;
+    for (int t = lane; t < P; t += 32) a[t] = t < len ? col[b + t] : INT_MAX;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = lane; t < P; t += 32) {
+          int u = t ^ j;
+          if (u > t) {
+            int x = a[t], y = a[u];
+            bool asc = (t & k) == 0;
+            if ((x > y) == asc) {
+              a[t] = y;
+              a[u] = x;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    for (int t = lane; t < len; t += 32) col[b + t] = a[t];
+    __syncwarp();
+  }
+}
+
+// tloc[e] = position of i inside row j for the entry e = (i, j).
+__global__ void k_tmap(const long long *row_ptr, const int32_t *col, int64_t n, uint16_t *tloc,
+                       DevStatus *st) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = wid; i < n; i += nwarps) {
+    const long long b = row_ptr[i], e1 = row_ptr[i + 1];
+    for (long long e = b + lane; e < e1; e += 32) {
+      const int j = col[e];
+      long long lo = row_ptr[j], hi = row_ptr[j + 1];
+      const long long rb = lo;
+      if (hi - rb > 65535) {
+        set_error(st, MAFP_ECAPACITY, hi - rb);
+        continue;
+      }
+      while (lo < hi) {
+        long long mid = (lo + hi) >> 1;
+        if (col[mid] < i) lo = mid + 1; else hi = mid;
+      }
+      tloc[e] = (uint16_t)(lo - rb);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host side
+template <typename T>
+static int build_neighbours_t(mafp_ctx *ctx, int64_t n, const void *pos_h, int64_t *row_ptr,
+                              int32_t *col, int64_t cap_nnz, int64_t *nnz_dev, int32_t *order,
+                              cudaStream_t s) {
+  using V = vec4_t<T>;
+  const V *pos = reinterpret_cast<const V *>(pos_h);
+  const int sms = sm_count();
+  const int nb_box = grid_for(n, kBoxThreads, kBoxBlocks);
+  MAFP_TIMED(ctx, s, "k_bbox<T>",
+             k_bbox<T><<<nb_box, kBoxThreads, 0, s>>>(pos, n, ctx->bbox_partial));
+  MAFP_TIMED(ctx, s, "k_grid",
+             k_grid<<<1, 32, 0, s>>>(ctx->bbox_partial, nb_box, ctx->d_grid, ctx->d_status, ctx->cap_cells));
+  MAFP_TIMED(ctx, s, "k_hash<T>",
+             k_hash<T><<<grid_for(n, 256, sms * 16), 256, 0, s>>>(pos, n, ctx->d_grid, ctx->keys_a,
+                                                       ctx->vals_a));
+  MAFP_TIMED(ctx, s, "k_clear_cells",
+             k_clear_cells<<<sms * 8, 256, 0, s>>>(ctx->d_grid, ctx->cell_start, ctx->cell_end,
+                                        ctx->n_ucell));
+  MAFP_LAUNCH_CHECK(ctx);
+  const int tiles = (int)((n + kRadixTile - 1) / kRadixTile);
+  uint32_t *kin = ctx->keys_a, *kout = ctx->keys_b;
+  int32_t *vin = ctx->vals_a, *vout = ctx->vals_b;
+  long long *offs = reinterpret_cast<long long *>(ctx->remap_i64);
+  for (int p = 0; p < ctx->radix_passes; ++p) {
+    MAFP_TIMED(ctx, s, "k_radix_hist",
+               k_radix_hist<<<tiles, kRadixThreads, 0, s>>>(kin, n, 8 * p, ctx->radix_hist, tiles,
+                                                  ctx->d_grid));
+    int rc = scan_i32_to_i64(ctx, ctx->radix_hist, offs, (int64_t)256 * tiles, s);
+    if (rc) return rc;
+    MAFP_TIMED(ctx, s, "k_radix_scatter",
+               k_radix_scatter<<<tiles, kRadixThreads, 0, s>>>(kin, vin, kout, vout, n, 8 * p, offs, tiles,
+                                                     ctx->d_grid));
+    MAFP_LAUNCH_CHECK(ctx);
+    uint32_t *tk = kin; kin = kout; kout = tk;
+    int32_t *tv = vin; vin = vout; vout = tv;
+  }
+  V *spos = reinterpret_cast<V *>(ctx->spos);
+  MAFP_TIMED(ctx, s, "k_cells<T>",
+             k_cells<T><<<grid_for(n, 256, sms * 16), 256, 0, s>>>(kin, vin, n, pos, spos, ctx->cell_start,
+                                                        ctx->cell_end, ctx->ucell, ctx->n_ucell,
+                                                        ctx->d_status, order, ctx->d_grid));
+  MAFP_TIMED(ctx, s, "k_identity_flag",
+             k_identity_flag<<<1, 1, 0, s>>>(ctx->d_status));
+  MAFP_LAUNCH_CHECK(ctx);
+  const int nbr_blocks = sms * 8;
+  MAFP_TIMED(ctx, s, "k_nbr<T,false>",
+             k_nbr<T, false><<<nbr_blocks, kNbrThreads, kNbrSmemBytes, s>>>(
+      ctx->d_grid, ctx->ucell, ctx->n_ucell, spos, vin, ctx->cell_start, ctx->cell_end,
+      ctx->counts, nullptr, nullptr, 0, n));
+  MAFP_LAUNCH_CHECK(ctx);
+  int rc = scan_i32_to_i64(ctx, ctx->counts, reinterpret_cast<long long *>(row_ptr), n, s);
+  if (rc) return rc;
+  MAFP_TIMED(ctx, s, "k_check_nnz",
+             k_check_nnz<<<1, 1, 0, s>>>(reinterpret_cast<const long long *>(row_ptr), n, cap_nnz, nnz_dev,
+                              ctx->d_status, ctx->d_grid));
+  MAFP_TIMED(ctx, s, "k_nbr<T,true>",
+             k_nbr<T, true><<<nbr_blocks, kNbrThreads, kNbrSmemBytes, s>>>(
+      ctx->d_grid, ctx->ucell, ctx->n_ucell, spos, vin, ctx->cell_start, ctx->cell_end,
+      ctx->counts, reinterpret_cast<const long long *>(row_ptr), col, cap_nnz, n));
+  MAFP_TIMED(ctx, s, "k_rowsort",
+             k_rowsort<<<grid_for(n, kSortWarps, sms * 8), kSortWarps * 32, 0, s>>>(
+      reinterpret_cast<const long long *>(row_ptr), col, n, cap_nnz, ctx->d_status));
+  MAFP_LAUNCH_CHECK(ctx);
+  return MAFP_OK;
+}
+
+int build_neighbours(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h,
+                     int64_t *row_ptr, int32_t *col, int64_t cap_nnz, int64_t *nnz_dev,
+                     int32_t *order, cudaStream_t s) {
+  if (dtype == MAFP_F64)
+    return build_neighbours_t<double>(ctx, n, pos_h, row_ptr, col, cap_nnz, nnz_dev, order, s);
+  return build_neighbours_t<float>(ctx, n, pos_h, row_ptr, col, cap_nnz, nnz_dev, order, s);
+}
+
+void init_kernel_attributes() {
+  cudaFuncSetAttribute(k_nbr<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kNbrSmemBytes);
+  cudaFuncSetAttribute(k_nbr<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kNbrSmemBytes);
+  cudaFuncSetAttribute(k_nbr<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kNbrSmemBytes);
+  cudaFuncSetAttribute(k_nbr<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kNbrSmemBytes);
+}
+
+int transpose_map(mafp_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                  uint16_t *tloc, cudaStream_t s) {
+  MAFP_TIMED(ctx, s, "k_tmap",
+             k_tmap<<<grid_for(n * 32, 256, sm_count() * 16), 256, 0, s>>>(
+      reinterpret_cast<const long long *>(row_ptr), col, n, tloc, ctx->d_status));
+  MAFP_LAUNCH_CHECK(ctx);
+  return MAFP_OK;
+}
+
+}  // namespace mafp

@@ -1,0 +1,405 @@
+// stencil.cu -- GFDM stencils of Eq. GFDM_Definition (Sec. 2.3), order 2.
+//
+// One group of G lanes per particle (G = 32 for 3D rows of ~180 entries, 8 for
+// 2D rows of ~40).  Lanes stride over the row, accumulate the packed moment
+// matrix A = sum_j w_j p_j p_j^T, reduce it with a reduce-scatter of shuffles,
+// factor it (Cholesky) and solve for the four right-hand sides in every lane.
+// FP32 path: one refinement step with the residual b - sum_j c_j p_j of the
+// rounded coefficients; particles whose Cholesky pivots are too small or whose
+// condition estimate exceeds cond_fp64 are queued and redone in FP64.
+#include "internal.cuh"
+
+namespace mafp {
+
+constexpr int kStThreads = 128;
+
+template <int M> struct Basis;
+template <> struct Basis<10> {
+  static constexpr int NA = 55;   // packed lower triangle of A
+  static constexpr int NR = 4;    // right-hand sides: d/dx, d/dy, d/dz, Laplacian
+};
+template <> struct Basis<6> {
+  static constexpr int NA = 21;
+  static constexpr int NR = 3;    // d/dxi, d/deta, surface Laplacian
+};
+
+__host__ __device__ constexpr int pad_to(int v, int g) { return ((v + g - 1) / g) * g; }
+__host__ __device__ constexpr int pk(int r, int c) { return r * (r + 1) / 2 + c; }
+
+template <typename C>
+struct StParams {
+  C alpha, ea, inv_den;   // W(s) = (exp(-alpha s^2) - ea) * inv_den, s <= 1
+  C piv_tol_rel;          // pivot <= tol * trace -> rank deficient (FP64) / fall back (FP32)
+  C cond_max;
+};
+
+template <typename C>
+__device__ __forceinline__ C weight_w(C s2, const StParams<C> &sp) {
+  return s2 <= C(1) ? (exp(-sp.alpha * s2) - sp.ea) * sp.inv_den : C(0);
+}
+
+// Monomial basis at one neighbour; returns w (0 for j outside the unit support).
+template <int M, typename C, typename V>
+__device__ __forceinline__ C basis_at(const V &xi, const V &xj, C hinv, const C (&t1)[3],
+                                      const C (&t2)[3], const StParams<C> &sp, C (&p)[M]) {
+  const C dx = C(xj.x) - C(xi.x), dy = C(xj.y) - C(xi.y), dz = C(xj.z) - C(xi.z);
+  const C s2 = ((dx * dx + dy * dy) + dz * dz) * (hinv * hinv);
+  const C w = weight_w<C>(s2, sp);
+  if constexpr (M == 10) {
+    const C qx = dx * hinv, qy = dy * hinv, qz = dz * hinv;
+    p[0] = C(1); p[1] = qx; p[2] = qy; p[3] = qz;
+    p[4] = qx * qx; p[5] = qy * qy; p[6] = qz * qz;
+    p[7] = qx * qy; p[8] = qx * qz; p[9] = qy * qz;
+  } else {
+    const C xi_ = (dx * t1[0] + dy * t1[1] + dz * t1[2]) * hinv;
+    const C et_ = (dx * t2[0] + dy * t2[1] + dz * t2[2]) * hinv;
+    p[0] = C(1); p[1] = xi_; p[2] = et_;
+    p[3] = xi_ * xi_; p[4] = xi_ * et_; p[5] = et_ * et_;
+  }
+  return w;
+}
+
+// Right-hand side k (unscaled: the 1/h and 1/h^2 factors are applied to the output).
+template <int M, typename C>
+__device__ __forceinline__ C rhs(int k, int r) {
+  if constexpr (M == 10) {
+    if (k < 3) return r == k + 1 ? C(1) : C(0);
+    return (r >= 4 && r <= 6) ? C(2) : C(0);
+  } else {
+    if (k < 2) return r == k + 1 ? C(1) : C(0);
+    return (r == 3 || r == 5) ? C(2) : C(0);
+  }
+}
+
+// In-register Cholesky of the packed matrix L (lower), returns false when a
+// pivot is <= tol.  invd gets 1/L_kk; pmin / pmax the extreme pivots.
+template <int M, typename C>
+__device__ __forceinline__ bool cholesky(C (&L)[Basis<M>::NA], C (&invd)[M], C tol, C &pmin,
+                                         C &pmax) {
+  pmin = C(INFINITY);
+  pmax = C(0);
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    C d = L[pk(k, k)];
+#pragma unroll
+    for (int l = 0; l < k; ++l) d -= L[pk(k, l)] * L[pk(k, l)];
+    ok = ok && (d > tol);
+    const C lkk = sqrt(d > tol ? d : C(1));
+    L[pk(k, k)] = lkk;
+    invd[k] = C(1) / lkk;
+    pmin = lkk < pmin ? lkk : pmin;
+    pmax = lkk > pmax ? lkk : pmax;
+#pragma unroll
+    for (int r = k + 1; r < M; ++r) {
+      C s = L[pk(r, k)];
+#pragma unroll
+      for (int l = 0; l < k; ++l) s -= L[pk(r, l)] * L[pk(k, l)];
+      L[pk(r, k)] = s * invd[k];
+    }
+  }
+  return ok;
+}
+
+template <int M, typename C>
+__device__ __forceinline__ void chol_solve(const C (&L)[Basis<M>::NA], const C (&invd)[M],
+                                           const C (&b)[M], C (&x)[M]) {
+  C y[M];
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+    C s = b[r];
+#pragma unroll
+    for (int l = 0; l < r; ++l) s -= L[pk(r, l)] * y[l];
+    y[r] = s * invd[r];
+  }
+#pragma unroll
+  for (int r = M - 1; r >= 0; --r) {
+    C s = y[r];
+#pragma unroll
+    for (int l = r + 1; l < M; ++l) s -= L[pk(l, r)] * x[l];
+    x[r] = s * invd[r];
+  }
+}
+
+// Process particle i with a group of G lanes.  Returns (through *result)
+//  0 = written, 1 = deficient (zeros written), 2 = queued for FP64.
+template <typename TS, typename C, int M, int G, bool REFINE, bool QUEUE>
+__device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *model,
+                                 const vec4_t<TS> *frame, const long long *row_ptr,
+                                 const int32_t *col, vec4_t<TS> *coef, const StParams<C> &sp,
+                                 C *sm /* per-group scratch, >= pad_to(NR*M or NA, G) */,
+                                 int *result, float *cond_out) {
+  constexpr int NA = Basis<M>::NA, NR = Basis<M>::NR;
+  constexpr int VA = pad_to(NA, G), VR = pad_to(NR * M, G);
+  using V = vec4_t<TS>;
+  const int lane = threadIdx.x & (G - 1);
+  const unsigned gm = group_mask<G>();
+  const V xi = ld4(pos + i);
+  const uint8_t mi = model[i];
+  const C hinv = C(1) / C(xi.w);
+  C t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0};
+  if constexpr (M == 6) {
+    const V f1 = ld4(frame + 2 * i), f3 = ld4(frame + 2 * i + 1);
+    t1[0] = C(f1.x); t1[1] = C(f1.y); t1[2] = C(f1.z);
+    const C n0 = C(f3.x), n1 = C(f3.y), n2 = C(f3.z);
+    t2[0] = n1 * t1[2] - n2 * t1[1];
+    t2[1] = n2 * t1[0] - n0 * t1[2];
+    t2[2] = n0 * t1[1] - n1 * t1[0];
+  }
+  const long long b = row_ptr[i], e1 = row_ptr[i + 1];
+  // ---- moments
+  C A[VA];
+#pragma unroll
+  for (int k = 0; k < VA; ++k) A[k] = C(0);
+  int cnt = 0;
+  for (long long e = b + lane; e < e1; e += G) {
+    const int j = col[e];
+    if (model[j] != mi) continue;
+    C p[M];
+    const C w = basis_at<M, C>(xi, ld4(pos + j), hinv, t1, t2, sp, p);
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+      const C wp = w * p[r];
+#pragma unroll
+      for (int c = 0; c <= r; ++c) A[pk(r, c)] += wp * p[c];
+    }
+    ++cnt;
+  }
+  cnt = group_sum<G>(cnt);
+  reduce_scatter<G, VA>(A);
+  __syncwarp(gm);
+#pragma unroll
+  for (int k = 0; k < VA / G; ++k) sm[lane * (VA / G) + k] = A[k];
+  __syncwarp(gm);
+  C L[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) L[k] = sm[k];
+  __syncwarp(gm);
+  C tr = 0;
+#pragma unroll
+  for (int r = 0; r < M; ++r) tr += L[pk(r, r)];
+  C invd[M], pmin, pmax;
+  const bool ok = (cnt >= M) && cholesky<M, C>(L, invd, sp.piv_tol_rel * tr, pmin, pmax);
+  const C cond = (pmax / pmin) * (pmax / pmin);
+  if (!ok || (QUEUE && !(cond <= sp.cond_max))) {
+    // deficient (decided in this precision unless queued) -> zeros
+    if (QUEUE && cnt >= M) {
+      *result = 2;
+      return;
+    }
+    for (long long e = b + lane; e < e1; e += G) st4(coef + e, mk4<TS>(0, 0, 0, 0));
+    *result = 1;
+    *cond_out = INFINITY;
+    return;
+  }
+  // ---- solve
+  C lam[NR][M];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    C bb[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) bb[r] = rhs<M, C>(k, r);
+    chol_solve<M, C>(L, invd, bb, lam[k]);
+  }
+  if constexpr (REFINE) {
+    // residual b - sum_j c_j p_j of the coefficients as they will be stored
+    C R[VR];
+#pragma unroll
+    for (int k = 0; k < VR; ++k) R[k] = C(0);
+    for (long long e = b + lane; e < e1; e += G) {
+      const int j = col[e];
+      if (model[j] != mi) continue;
+      C p[M];
+      const C w = basis_at<M, C>(xi, ld4(pos + j), hinv, t1, t2, sp, p);
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        C s = 0;
+#pragma unroll
+        for (int r = 0; r < M; ++r) s += p[r] * lam[k][r];
+        const C c = w * s;
+#pragma unroll
+        for (int r = 0; r < M; ++r) R[k * M + r] += c * p[r];
+      }
+    }
+    reduce_scatter<G, VR>(R);
+#pragma unroll
+    for (int k = 0; k < VR / G; ++k) sm[lane * (VR / G) + k] = R[k];
+    __syncwarp(gm);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      C rr[M], d[M];
+#pragma unroll
+      for (int r = 0; r < M; ++r) rr[r] = rhs<M, C>(k, r) - sm[k * M + r];
+      chol_solve<M, C>(L, invd, rr, d);
+#pragma unroll
+      for (int r = 0; r < M; ++r) lam[k][r] += d[r];
+    }
+    __syncwarp(gm);
+  }
+  // ---- coefficients
+  const C h2inv = hinv * hinv;
+  for (long long e = b + lane; e < e1; e += G) {
+    const int j = col[e];
+    vec4_t<TS> out = mk4<TS>(0, 0, 0, 0);
+    if (model[j] == mi) {
+      C p[M];
+      const C w = basis_at<M, C>(xi, ld4(pos + j), hinv, t1, t2, sp, p);
+      C c[NR];
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        C s = 0;
+#pragma unroll
+        for (int r = 0; r < M; ++r) s += p[r] * lam[k][r];
+        c[k] = w * s;
+      }
+      if constexpr (M == 10) {
+        out = mk4<TS>(TS(c[0] * hinv), TS(c[1] * hinv), TS(c[2] * hinv), TS(c[3] * h2inv));
+      } else {
+        const C gx = (c[0] * t1[0] + c[1] * t2[0]) * hinv;
+        const C gy = (c[0] * t1[1] + c[1] * t2[1]) * hinv;
+        const C gz = (c[0] * t1[2] + c[1] * t2[2]) * hinv;
+        out = mk4<TS>(TS(gx), TS(gy), TS(gz), TS(c[2] * h2inv));
+      }
+    }
+    st4(coef + e, out);
+  }
+  *result = 0;
+  *cond_out = (float)cond;
+}
+
+// Main kernel: every particle of model (M == 10 ? 3D : 2D).
+template <typename TS, typename C, int M, int G, bool REFINE, bool QUEUE>
+__global__ void __launch_bounds__(kStThreads) k_stencil(
+    int64_t n, const vec4_t<TS> *pos, const uint8_t *model, const vec4_t<TS> *frame,
+    const long long *row_ptr, const int32_t *col, vec4_t<TS> *coef, uint8_t *status,
+    float *cond, StParams<C> sp, DevStatus *st, int32_t *queue) {
+  constexpr int NA = Basis<M>::NA, NR = Basis<M>::NR;
+  constexpr int SMG = pad_to(NA, G) > pad_to(NR * M, G) ? pad_to(NA, G) : pad_to(NR * M, G);
+  __shared__ C smem[(kStThreads / G) * SMG];
+  const int grp = threadIdx.x / G;
+  C *sm = smem + grp * SMG;
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const uint8_t want = M == 10 ? MAFP_MODEL_3D : MAFP_MODEL_2D;
+  for (int64_t i = gid; i < n; i += ngroups) {
+    if (model[i] != want) continue;   // uniform within the group
+    int res;
+    float cd = 0.0f;
+    stencil_particle<TS, C, M, G, REFINE, QUEUE>(i, pos, model, frame, row_ptr, col, coef, sp,
+                                                 sm, &res, &cd);
+    if (lane == 0) {
+      if (res == 2) {
+        const int slot = atomicAdd(&st->fallback_count, 1);
+        queue[slot] = (int32_t)i;
+      } else {
+        status[i] = res == 0 ? MAFP_STENCIL_OK : MAFP_STENCIL_DEFICIENT;
+        cond[i] = res == 0 ? cd : INFINITY;
+        if (res == 1) inc_ll(&st->n_deficient);
+      }
+    }
+  }
+}
+
+// FP64 redo of the queued particles of one model (FP32 storage).
+template <int M, int G>
+__global__ void __launch_bounds__(kStThreads) k_stencil_redo(
+    const float4 *pos, const uint8_t *model, const float4 *frame, const long long *row_ptr,
+    const int32_t *col, float4 *coef, uint8_t *status, float *cond, StParams<double> sp,
+    DevStatus *st, const int32_t *queue) {
+  constexpr int NA = Basis<M>::NA, NR = Basis<M>::NR;
+  constexpr int SMG = pad_to(NA, G) > pad_to(NR * M, G) ? pad_to(NA, G) : pad_to(NR * M, G);
+  __shared__ double smem[(kStThreads / G) * SMG];
+  const int grp = threadIdx.x / G;
+  double *sm = smem + grp * SMG;
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int nq = st->fallback_count;
+  const uint8_t want = M == 10 ? MAFP_MODEL_3D : MAFP_MODEL_2D;
+  for (int64_t q = gid; q < nq; q += ngroups) {
+    const int64_t i = queue[q];
+    if (model[i] != want) continue;
+    int res;
+    float cd = 0.0f;
+    stencil_particle<float, double, M, G, false, false>(i, pos, model, frame, row_ptr, col, coef,
+                                                         sp, sm, &res, &cd);
+    if (lane == 0) {
+      status[i] = res == 0 ? MAFP_STENCIL_FP64 : MAFP_STENCIL_DEFICIENT;
+      cond[i] = res == 0 ? cd : INFINITY;
+      if (res == 1) inc_ll(&st->n_deficient);
+      else inc_ll(&st->n_fp64_stencil);
+    }
+  }
+}
+
+__global__ void k_reset_queue(DevStatus *st) { st->fallback_count = 0; }
+
+template <typename C>
+static StParams<C> make_params(const mafp_params &p, double piv_tol) {
+  StParams<C> sp;
+  const double ea = exp(-p.alpha_w);
+  sp.alpha = (C)p.alpha_w;
+  sp.ea = (C)ea;
+  sp.inv_den = (C)(1.0 / (1.0 - ea));
+  sp.piv_tol_rel = (C)piv_tol;
+  sp.cond_max = (C)p.cond_fp64;
+  return sp;
+}
+
+int build_stencils(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h,
+                   const uint8_t *model, const void *frame, const int64_t *row_ptr,
+                   const int32_t *col, void *coef, uint8_t *status, float *cond, cudaStream_t s) {
+  const long long *rp = reinterpret_cast<const long long *>(row_ptr);
+  const int sms = sm_count();
+  const int b3 = grid_for(n * 32, kStThreads, sms * 64);
+  const int b2 = grid_for(n * 8, kStThreads, sms * 64);
+  if (dtype == MAFP_F64) {
+    const StParams<double> sp = make_params<double>(ctx->prm, 1e-12);
+    MAFP_TIMED(ctx, s, "k_stencil<double,double,10,32,false,false>",
+               k_stencil<double, double, 10, 32, false, false><<<b3, kStThreads, 0, s>>>(
+        n, (const double4_16a *)pos_h, model, (const double4_16a *)frame, rp, col, (double4_16a *)coef,
+        status, cond, sp, ctx->d_status, ctx->fallback));
+    MAFP_TIMED(ctx, s, "k_stencil<double,double,6,8,false,false>",
+               k_stencil<double, double, 6, 8, false, false><<<b2, kStThreads, 0, s>>>(
+        n, (const double4_16a *)pos_h, model, (const double4_16a *)frame, rp, col, (double4_16a *)coef,
+        status, cond, sp, ctx->d_status, ctx->fallback));
+    MAFP_LAUNCH_CHECK(ctx);
+    return MAFP_OK;
+  }
+  const StParams<float> sp = make_params<float>(ctx->prm, 1e-6);
+  const StParams<double> sp64 = make_params<double>(ctx->prm, 1e-12);
+  MAFP_TIMED(ctx, s, "k_reset_queue",
+             k_reset_queue<<<1, 1, 0, s>>>(ctx->d_status));
+  if (dtype == MAFP_F32_PLAIN) {
+    MAFP_TIMED(ctx, s, "k_stencil<float,float,10,32,false,true>",
+               k_stencil<float, float, 10, 32, false, true><<<b3, kStThreads, 0, s>>>(
+        n, (const float4 *)pos_h, model, (const float4 *)frame, rp, col, (float4 *)coef, status,
+        cond, sp, ctx->d_status, ctx->fallback));
+    MAFP_TIMED(ctx, s, "k_stencil<float,float,6,8,false,true>",
+               k_stencil<float, float, 6, 8, false, true><<<b2, kStThreads, 0, s>>>(
+        n, (const float4 *)pos_h, model, (const float4 *)frame, rp, col, (float4 *)coef, status,
+        cond, sp, ctx->d_status, ctx->fallback));
+  } else {
+    MAFP_TIMED(ctx, s, "k_stencil<float,float,10,32,true,true>",
+               k_stencil<float, float, 10, 32, true, true><<<b3, kStThreads, 0, s>>>(
+        n, (const float4 *)pos_h, model, (const float4 *)frame, rp, col, (float4 *)coef, status,
+        cond, sp, ctx->d_status, ctx->fallback));
+    MAFP_TIMED(ctx, s, "k_stencil<float,float,6,8,true,true>",
+               k_stencil<float, float, 6, 8, true, true><<<b2, kStThreads, 0, s>>>(
+        n, (const float4 *)pos_h, model, (const float4 *)frame, rp, col, (float4 *)coef, status,
+        cond, sp, ctx->d_status, ctx->fallback));
+  }
+  MAFP_TIMED(ctx, s, "k_stencil_redo<10,32>",
+             k_stencil_redo<10, 32><<<sms * 4, kStThreads, 0, s>>>(
+      (const float4 *)pos_h, model, (const float4 *)frame, rp, col, (float4 *)coef, status, cond,
+      sp64, ctx->d_status, ctx->fallback));
+  MAFP_TIMED(ctx, s, "k_stencil_redo<6,8>",
+             k_stencil_redo<6, 8><<<sms * 4, kStThreads, 0, s>>>(
+      (const float4 *)pos_h, model, (const float4 *)frame, rp, col, (float4 *)coef, status, cond,
+      sp64, ctx->d_status, ctx->fallback));
+  MAFP_LAUNCH_CHECK(ctx);
+  return MAFP_OK;
+}
+
+}  // namespace mafp

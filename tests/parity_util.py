@@ -1,0 +1,83 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI
+and compare with the oracle.
+
+Error measures (derived in the design notes from FP32 arithmetic):
+  stencils  -- per row and operator, max_e |a_e - b_e| / max_e |b_e|
+  outputs   -- per output column (field, operator), max_i |a_i - b_i| / max_i |b_i|
+Storing inputs and coefficients in FP32 perturbs every output by up to
+u * sum_j |c_ij| |u_j - u_i| (u = 2^-24), which for the Laplacian reaches
+~1e-5 of the column maximum, so the 1e-4 bar is stated normwise; the
+componentwise error (floor 1e-3 of the column maximum) is reported too.
+"""
+import numpy as np
+import torch
+
+from paper_2405_13165_gb300 import mafp as M
+from paper_2405_13165_gb300.pipeline import Pipeline, cloud_to_device
+
+TOL = {M.F32_REFINED: 1e-4, M.F32_PLAIN: 2e-3, M.F64: 1e-10}
+
+
+def run_gpu(cloud, dtype, cap_nnz=None, ctx=None, stages=("nbr", "cls", "st", "ap")):
+    n = cloud.n
+    ctx = ctx or M.Context(max(n, 1))
+    cap_nnz = cap_nnz or max(400 * n, 16)
+    pipe = Pipeline(ctx, max(n, 1), cap_nnz, dtype)
+    d = cloud_to_device(cloud, dtype)
+    ctx.reset_status()
+    if "nbr" in stages:
+        pipe.neighbours(d, with_order=True)
+    if "cls" in stages:
+        pipe.classify(d)
+    if "st" in stages:
+        pipe.stencils(d)
+    if "ap" in stages:
+        pipe.apply(d)
+    torch.cuda.synchronize()
+    st = ctx.status()
+    nnz = int(pipe.row_ptr[n].item())
+    res = dict(status_block=st, row_ptr=pipe.row_ptr[: n + 1].cpu().numpy(),
+               col=pipe.col[:nnz].cpu().numpy(), order=pipe.order[:n].cpu().numpy(),
+               flag=pipe.flag[:n].cpu().numpy(), preflag=pipe.preflag[:n].cpu().numpy(),
+               near=pipe.near[:n].cpu().numpy(), eig=pipe.eig[:n].double().cpu().numpy(),
+               frame=pipe.frame[:n].double().cpu().numpy(),
+               hfilm=pipe.hfilm[:n].double().cpu().numpy(),
+               coef=pipe.coef[:nnz].double().cpu().numpy(),
+               status=pipe.status[:n].cpu().numpy(), cond=pipe.cond[:n].cpu().numpy(),
+               out=pipe.out[:n].double().cpu().numpy())
+    return res, pipe, d, ctx
+
+
+def stencil_rowwise_error(rp, a, b, rows=None):
+    """max over rows of max_e |a-b| / max_e |b| per operator (rows with b == 0 skipped)."""
+    rows = range(len(rp) - 1) if rows is None else rows
+    worst = np.zeros(4)
+    for i in rows:
+        s = slice(rp[i], rp[i + 1])
+        bb = np.abs(b[s]).max(0) if rp[i + 1] > rp[i] else np.zeros(4)
+        d = np.abs(a[s] - b[s]).max(0) if rp[i + 1] > rp[i] else np.zeros(4)
+        ok = bb > 0
+        worst[ok] = np.maximum(worst[ok], d[ok] / bb[ok])
+        worst[~ok] = np.maximum(worst[~ok], d[~ok])
+    return worst
+
+
+def stencil_rowwise_error_vec(rp, a, b):
+    """Vectorised form of stencil_rowwise_error over all rows."""
+    n = len(rp) - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    bmax = np.zeros((n, 4))
+    dmax = np.zeros((n, 4))
+    np.maximum.at(bmax, rows, np.abs(b))
+    np.maximum.at(dmax, rows, np.abs(a - b))
+    rel = np.where(bmax > 0, dmax / np.where(bmax > 0, bmax, 1), dmax)
+    return rel.max(0) if n else np.zeros(4), rel
+
+
+def column_error(a, b):
+    """Normwise error per output column and the componentwise p99 (floor 1e-3)."""
+    scale = np.abs(b).reshape(-1, 16).max(0)
+    diff = np.abs(a - b).reshape(-1, 16)
+    normwise = diff.max(0) / np.where(scale > 0, scale, 1)
+    comp = diff / np.maximum(np.abs(b).reshape(-1, 16), 1e-3 * scale)
+    return normwise, np.percentile(comp, 99, axis=0) if comp.size else np.zeros(16)
