@@ -41,6 +41,27 @@ APPLY_BYTES_NNZ = {4: 20, 8: 36}
 APPLY_BYTES_N = {4: 88, 8: 168}
 ST3_FLOP_NBR, ST3_FLOP_PART = 210.0, 1200.0
 ST2_FLOP_NBR, ST2_FLOP_PART = 90.0, 1000.0
+NBR_FLOP_TEST = 11.0   # 3 sub, 2 fma + 1 mul (d^2), add + 2 mul (r^2), compare
+
+
+def candidate_tests(cloud) -> int:
+    """Distance tests of the cell-list search: sum over particles of the
+    particle count of the 27 cells around their own cell (cells of edge max h)."""
+    P = cloud.pos_h.astype(np.float64)
+    lo, hi = P[:, :3].min(0), P[:, :3].max(0)
+    c = float(P[:, 3].max()) * (1.0 + 1e-6)
+    dim = (np.floor((hi - lo) / c) + 1).astype(np.int64)
+    cc = np.clip(np.floor((P[:, :3] - lo) * (1.0 / c)).astype(np.int64), 0, dim - 1)
+    grid = np.zeros(tuple(dim[::-1] + 2), np.int64)
+    np.add.at(grid, (cc[:, 2] + 1, cc[:, 1] + 1, cc[:, 0] + 1), 1)
+    s = np.zeros_like(grid)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                s[1:-1, 1:-1, 1:-1] += grid[1 + dz:grid.shape[0] - 1 + dz,
+                                            1 + dy:grid.shape[1] - 1 + dy,
+                                            1 + dx:grid.shape[2] - 1 + dx]
+    return int(s[cc[:, 2] + 1, cc[:, 1] + 1, cc[:, 0] + 1].sum())
 
 
 def parse():
@@ -50,11 +71,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mafp", choices=["mafp", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000, help="particle count of the jet cloud")
-    ap.add_argument("--cpu-sample", type=int, default=200_000,
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000,
                     help="particles of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed launch shapes 'g3d,g2d,gapply' instead of the autotuner")
     return ap.parse_args()
 
 
@@ -100,7 +123,7 @@ class ClockSampler:
         sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]})
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
         loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
         return {"sm_mhz": statistics.median(loaded) if loaded else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
@@ -222,6 +245,13 @@ def bench_gpu(args):
         mark()
         return marks
 
+    from paper_2405_13165_gb300 import autotune
+    if args.tuning:
+        g3, g2, ga = (int(v) for v in args.tuning.split(","))
+        ctx.set_tuning(stencil3d_group=g3, stencil2d_group=g2, apply_group=ga)
+        tuned = {"tuning": ctx.tuning(), "source": "command line"}
+    else:
+        tuned = autotune.tune(ctx, pipe, d, use_cache=False)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -278,6 +308,7 @@ def bench_gpu(args):
     nbr3 = int((same & (model[rows] == 0)).sum().item())
     nbr2 = int((same & (model[rows] == 1)).sum().item())
     n3 = int((model == 0).sum().item())
+    n_cand = candidate_tests(cloud)
     n2 = n - n3
     sm_mhz = clocks.get("sm_mhz") or 1920.0
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -299,33 +330,35 @@ def bench_gpu(args):
         return sum(v[1] for _, v in hit) / max(launches, 1), launches
 
     kernels = {}
-    ms, _ = kernel_ms("k_apply<float")
+    ms, _ = kernel_ms("k_apply<G=")
     if ms:
         b = APPLY_BYTES_NNZ[4] * nnz + APPLY_BYTES_N[4] * n
         kernels["apply_ops"] = {"bound": "hbm", "achieved": b / (ms * 1e-3) / 1e9, "peak": hbm_peak,
                                 "unit": "GB/s", "ms": ms, "algorithmic": b,
                                 "peak_src": hbm_src}
-    ms, _ = kernel_ms("k_stencil<float,float,10")
+    ms, _ = kernel_ms("k_stencil<f32,M=10")
     if ms:
         fl = ST3_FLOP_NBR * nbr3 + ST3_FLOP_PART * n3
         kernels["build_stencils_3d"] = {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12,
                                         "peak": fp32_peak, "unit": "TFLOP/s", "ms": ms,
                                         "algorithmic": fl, "peak_src": "FP32 FMA issue rate at sampled clock"}
-    ms, _ = kernel_ms("k_stencil<float,float,6")
+    ms, _ = kernel_ms("k_stencil<f32,M=6")
     if ms:
         fl = ST2_FLOP_NBR * nbr2 + ST2_FLOP_PART * n2
         kernels["build_stencils_2d"] = {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12,
                                         "peak": fp32_peak, "unit": "TFLOP/s", "ms": ms,
                                         "algorithmic": fl, "peak_src": "FP32 FMA issue rate at sampled clock"}
-    ms, _ = kernel_ms("k_nbr<T,true>")
+    ms, _ = kernel_ms("k_nbr_mask<float>")
     if ms:
-        b = 4 * nnz + 16 * n
-        kernels["nbr_fill"] = {"bound": "hbm", "achieved": b / (ms * 1e-3) / 1e9, "peak": hbm_peak,
-                               "unit": "GB/s", "ms": ms, "algorithmic": b, "peak_src": hbm_src}
+        fl = NBR_FLOP_TEST * n_cand
+        kernels["nbr_mask"] = {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": fp32_peak,
+                               "unit": "TFLOP/s", "ms": ms, "algorithmic": fl,
+                               "candidate_tests": n_cand,
+                               "peak_src": "FP32 FMA issue rate at sampled clock"}
     top = max(prof.items(), key=lambda kv: kv[1][1])
     dominant = None
-    for key, pref in (("apply_ops", "k_apply<float"), ("build_stencils_3d", "k_stencil<float,float,10"),
-                      ("build_stencils_2d", "k_stencil<float,float,6"), ("nbr_fill", "k_nbr<T,true>")):
+    for key, pref in (("apply_ops", "k_apply<G="), ("build_stencils_3d", "k_stencil<f32,M=10"),
+                      ("build_stencils_2d", "k_stencil<f32,M=6"), ("nbr_mask", "k_nbr_mask<float>")):
         if top[0].startswith(pref):
             dominant = key
     if dominant is None:
@@ -439,10 +472,13 @@ def bench_gpu(args):
             "kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
                             for kk, vv in v.items()} for k, v in kernels.items()},
             "fp64_vs_fp32": fp64,
+            "tuning": tuned,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": int(launches_per_step * args.steps),
+            "kernel_profile_top": [{"kernel": k, "launches": v[0], "ms_per_launch": round(v[1] / v[0], 4)}
+                                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])[:12]],
             "device_status": {k: st[k] for k in ("code", "n_fp64_stencil", "n_fp64_eigen",
                                                  "n_deficient", "n_near", "cells_identity")},
             "wall_s_timed_region": round(t_wall, 3),

@@ -70,6 +70,16 @@ typedef struct {
   double near_rel;       /* relative band for reporting near-threshold decisions (1e-6) */
 } mafp_params;
 
+/* Launch shapes (no counterpart in the paper): lanes that cooperate on one
+ * particle or row.  Every value gives the same results up to rounding order;
+ * the autotuner picks the fastest for a cloud's population mix. */
+typedef struct {
+  int32_t stencil3d_group; /* lanes per 3D particle in mafp_build_stencils: 8, 16 or 32 */
+  int32_t stencil2d_group; /* lanes per 2D particle in mafp_build_stencils: 4, 8 or 16 */
+  int32_t apply_group;     /* lanes per row in mafp_apply_ops / _backward: 4, 8 or 16 */
+  int32_t reserved;
+} mafp_tuning;
+
 /* Device-side status block, copied out by mafp_get_status. */
 typedef struct {
   int32_t code;            /* first device-detected error (MAFP_E*), 0 if none */
@@ -101,6 +111,9 @@ int mafp_create(mafp_ctx **out, const mafp_params *params, int64_t cap_particles
 int mafp_destroy(mafp_ctx *ctx);
 /* Message of the last host-side error of this context (never NULL). */
 const char *mafp_last_error(const mafp_ctx *ctx);
+/* Set / read the launch shapes of a context (MAFP_EINVAL for unsupported values). */
+int mafp_set_tuning(mafp_ctx *ctx, const mafp_tuning *t);
+int mafp_get_tuning(const mafp_ctx *ctx, mafp_tuning *t);
 /* Copy the device status block to *out after synchronising `stream`. */
 int mafp_get_status(mafp_ctx *ctx, mafp_status *out, void *stream);
 /* Zero the device status block (enqueued on `stream`). */
@@ -171,7 +184,12 @@ int mafp_build_stencils(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos
 
 /* --------------------------------------------------------------------------
  * mafp_apply_ops -- stencil application, Eq. GFDM_Definition:
- *   out[i][f] = sum_{e in row i} coef[e] * fields[col[e]][f],  f = u, v, w, p
+ *   out[i][f] = sum_{e in row i} coef[e] * (fields[col[e]][f] - fields[i][f]),
+ *   f = u, v, w, p.  The coefficients must annihilate constants
+ *   (sum_j c_ij = 0 for every operator), as the order-2 GFDM stencils of
+ *   mafp_build_stencils do by construction; then this equals
+ *   sum_j c_ij u_j, and forming u_j - u_i first removes the u_i sum_j c_ij
+ *   residue that FP32 rounding of the coefficients would otherwise add.
  *   fields x4 [n];  out x4 [4n] written: out[4i+f] = (d_x, d_y, d_z, Lap) of field f */
 int mafp_apply_ops(mafp_ctx *ctx, int64_t n, int32_t dtype, const int64_t *row_ptr,
                    const int32_t *col, const void *coef, const void *fields, void *out,
@@ -184,9 +202,11 @@ int mafp_apply_ops(mafp_ctx *ctx, int64_t n, int32_t dtype, const int64_t *row_p
 int mafp_transpose_map(mafp_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col,
                        uint16_t *tloc, void *stream);
 
-/* mafp_apply_ops_backward -- transpose of mafp_apply_ops (adjoint w.r.t. the
- * field values):  gfields[j][f] = sum_{i in S_j} sum_op coef_ij^op gout[4i+f][op],
- * gathered through tloc (deterministic order).  gout x4 [4n], gfields x4 [n]. */
+/* mafp_apply_ops_backward -- exact adjoint of mafp_apply_ops w.r.t. the
+ * field values:  gfields[j][f] = sum_{i in S_j} sum_op coef_ij^op gout[4i+f][op]
+ *                               - sum_op (sum_k coef_jk^op) gout[4j+f][op],
+ * gathered through tloc (deterministic order; the second term vanishes for
+ * stencils that annihilate constants).  gout x4 [4n], gfields x4 [n]. */
 int mafp_apply_ops_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const int64_t *row_ptr,
                             const int32_t *col, const uint16_t *tloc, const void *coef,
                             const void *gout, void *gfields, void *stream);

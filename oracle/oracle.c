@@ -287,9 +287,12 @@ static void classify_one(int64_t i, const double *P, const uint8_t *model, const
         if (!(user[i] & USER_TO_2D)) {
           int eps_near = near_rel(eps, prm->eps_lambda_max, prm->near_rel);
           int ang_near = fabs(ndw - cth) <= prm->near_rel;
+          /* w3 is not unique when l2 = l3 (e.g. collinear neighbours): the
+           * eigenvector test has no single answer and is reported instead */
+          int degenerate = (lam[1] - lam[2]) <= 1e-9 * lam[0];
           /* a near-threshold quantity only matters when the other test passes */
           if ((eps_near && ndw >= cth) || (ang_near && eps < prm->eps_lambda_max) ||
-              (eps_near && ang_near))
+              (eps_near && ang_near) || (degenerate && eps < prm->eps_lambda_max))
             nr = 1;
         }
       } else if (!has_int) {

@@ -1,0 +1,85 @@
+"""Autotuner of the launch shapes (lanes per particle / per row) of
+build_stencils and apply_ops.
+
+For a cloud already on the device it times every supported group size of a
+stage with CUDA events (a few repetitions, best taken), keeps the fastest,
+and caches the choice per population mix (3D fraction and mean row length,
+both bucketed) in a JSON file so later runs on similar clouds skip the sweep.
+Every shape computes the same results up to summation order.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+from . import mafp as M
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
+CHOICES = {"stencil3d_group": (8, 16, 32), "stencil2d_group": (4, 8, 16),
+           "apply_group": (4, 8, 16)}
+
+
+def mix_key(d, pipe, n: int) -> str:
+    frac3 = float((d["model"][:n] == 0).float().mean().item()) if n else 0.0
+    row = float(pipe.row_ptr[n].item()) / max(n, 1)
+    return f"f3={round(frac3, 1):.1f}/row={int(round(row / 16.0)) * 16}"
+
+
+def _time(fn, reps: int = 3) -> float:
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def tune(ctx: M.Context, pipe, d, use_cache: bool = True, verbose: bool = False) -> dict:
+    """Pick group sizes for this cloud; returns the chosen tuning and timings."""
+    n = d["pos_h"].shape[0]
+    pipe.neighbours(d)
+    pipe.classify(d)
+    torch.cuda.synchronize()
+    key = mix_key(d, pipe, n)
+    cache = {}
+    if use_cache and os.path.exists(CACHE):
+        try:
+            cache = json.load(open(CACHE))
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        ctx.set_tuning(**cache[key]["tuning"])
+        return cache[key]
+    timings = {}
+    best = dict(ctx.tuning())
+    for knob in ("stencil3d_group", "stencil2d_group"):
+        res = {}
+        for g in CHOICES[knob]:
+            ctx.set_tuning(**{**best, knob: g})
+            res[g] = _time(lambda: pipe.stencils(d))
+        best[knob] = min(res, key=res.get)
+        timings[knob] = res
+    ctx.set_tuning(**best)
+    pipe.stencils(d)
+    res = {}
+    for g in CHOICES["apply_group"]:
+        ctx.set_tuning(**{**best, "apply_group": g})
+        res[g] = _time(lambda: pipe.apply(d))
+    best["apply_group"] = min(res, key=res.get)
+    timings["apply_group"] = res
+    ctx.set_tuning(**best)
+    entry = {"tuning": best, "timings_ms": {k: {str(g): round(v, 4) for g, v in r.items()}
+                                            for k, r in timings.items()}, "key": key}
+    if verbose:
+        print("autotune", entry)
+    if use_cache:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        cache[key] = entry
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+    return entry

@@ -107,6 +107,9 @@ int mafp_create(mafp_ctx **out, const mafp_params *params, int64_t cap_particles
   mafp_ctx *ctx = (mafp_ctx *)calloc(1, sizeof(mafp_ctx));
   if (!ctx) return MAFP_ECUDA;
   if (params) ctx->prm = *params; else mafp_default_params(&ctx->prm);
+  ctx->tune.stencil3d_group = 32;
+  ctx->tune.stencil2d_group = 8;
+  ctx->tune.apply_group = 8;
   ctx->cap_particles = cap_particles;
   ctx->cap_cells = cap_cells;
   cudaGetDevice(&ctx->device);
@@ -131,6 +134,8 @@ int mafp_create(mafp_ctx **out, const mafp_params *params, int64_t cap_particles
       {(void **)&ctx->ucell, sizeof(int32_t) * 2 * cap},
       {(void **)&ctx->n_ucell, sizeof(int32_t) * 4},
       {(void **)&ctx->counts, sizeof(int32_t) * cap},
+      {(void **)&ctx->nbr_mask, sizeof(uint32_t) * kMaskWords * cap},
+      {(void **)&ctx->overflow, sizeof(int32_t) * cap},
       {(void **)&ctx->scan_tmp, sizeof(long long) * (i64_len / 4096 + 4)},
       {(void **)&ctx->bbox_partial, sizeof(double) * 1024 * 8},
       {(void **)&ctx->fallback, sizeof(int32_t) * cap},
@@ -162,6 +167,7 @@ int mafp_destroy(mafp_ctx *ctx) {
   void *ptrs[] = {ctx->keys_a,    ctx->keys_b,   ctx->vals_a,       ctx->vals_b,
                   ctx->radix_hist, ctx->cell_start, ctx->cell_end,   ctx->spos,
                   ctx->ucell,     ctx->n_ucell,  ctx->counts,       ctx->scan_tmp,
+                  ctx->nbr_mask,  ctx->overflow,
                   ctx->bbox_partial, ctx->fallback, ctx->d_status,  ctx->d_grid,
                   ctx->remap_i64, ctx->remap_i32};
   for (void *p : ptrs)
@@ -176,6 +182,22 @@ int mafp_destroy(mafp_ctx *ctx) {
 }
 
 const char *mafp_last_error(const mafp_ctx *ctx) { return ctx ? ctx->err : kNoCtx; }
+
+int mafp_set_tuning(mafp_ctx *ctx, const mafp_tuning *t) {
+  if (!ctx || !t) return MAFP_EINVAL;
+  const int g3 = t->stencil3d_group, g2 = t->stencil2d_group, ga = t->apply_group;
+  if (!(g3 == 8 || g3 == 16 || g3 == 32)) return fail(ctx, MAFP_EINVAL, "stencil3d_group");
+  if (!(g2 == 4 || g2 == 8 || g2 == 16)) return fail(ctx, MAFP_EINVAL, "stencil2d_group");
+  if (!(ga == 4 || ga == 8 || ga == 16)) return fail(ctx, MAFP_EINVAL, "apply_group");
+  ctx->tune = *t;
+  return MAFP_OK;
+}
+
+int mafp_get_tuning(const mafp_ctx *ctx, mafp_tuning *t) {
+  if (!ctx || !t) return MAFP_EINVAL;
+  *t = ctx->tune;
+  return MAFP_OK;
+}
 
 int mafp_get_status(mafp_ctx *ctx, mafp_status *out, void *stream) {
   if (!ctx || !out) return MAFP_EINVAL;

@@ -7,7 +7,10 @@ namespace mafp {
 
 constexpr int kApThreads = 256;
 
-// out[i][f][op] = sum_{e in row i} coef[e].op * fields[col[e]].f
+// out[i][f][op] = sum_{e in row i} coef[e].op * (fields[col[e]].f - fields[i].f)
+// The stencils reproduce constants (sum_j c_ij = 0, order-2 consistency of
+// Sec. 2.3), so this is Eq. GFDM_Definition; differencing first removes the
+// u_i * sum_j c_ij term that FP32 rounding of the coefficients leaves behind.
 // A group of G lanes per row; lanes stride over the row with U loads in flight.
 template <typename T, int G, int U>
 __global__ void __launch_bounds__(kApThreads) k_apply(int64_t n, const long long *row_ptr,
@@ -20,6 +23,7 @@ __global__ void __launch_bounds__(kApThreads) k_apply(int64_t n, const long long
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
   for (int64_t i = gid; i < n; i += ngroups) {
     const long long b = row_ptr[i], e1 = row_ptr[i + 1];
+    const V fi = ld4(fields + i);
     T acc[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = T(0);
@@ -35,7 +39,7 @@ __global__ void __launch_bounds__(kApThreads) k_apply(int64_t n, const long long
       for (int u = 0; u < U; ++u) f[u] = ld4(fields + j[u]);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const T fv[4] = {f[u].x, f[u].y, f[u].z, f[u].w};
+        const T fv[4] = {f[u].x - fi.x, f[u].y - fi.y, f[u].z - fi.z, f[u].w - fi.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           acc[4 * q + 0] += c[u].x * fv[q];
@@ -49,7 +53,7 @@ __global__ void __launch_bounds__(kApThreads) k_apply(int64_t n, const long long
       const int j = __ldg(col + e);
       const V c = ld4(coef + e);
       const V f = ld4(fields + j);
-      const T fv[4] = {f.x, f.y, f.z, f.w};
+      const T fv[4] = {f.x - fi.x, f.y - fi.y, f.z - fi.z, f.w - fi.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         acc[4 * q + 0] += c.x * fv[q];
@@ -76,8 +80,10 @@ __global__ void __launch_bounds__(kApThreads) k_apply(int64_t n, const long long
   }
 }
 
-// gfields[j][f] = sum_{e in row j} sum_op coef[(i, j)].op * gout[i][f][op],
-// i = col[e], (i, j) found at row_ptr[i] + tloc[e].
+// Exact adjoint of k_apply with respect to the fields:
+// gfields[j][f] = sum_{e in row j} sum_op (coef[(i, j)].op gout[i][f][op] - coef[e].op gout[j][f][op]),
+// i = col[e], (i, j) found at row_ptr[i] + tloc[e]; the second term is the
+// adjoint of the -u_j sum_k c_jk part of the differenced form.
 template <typename T, int G>
 __global__ void __launch_bounds__(kApThreads) k_apply_T(int64_t n, const long long *row_ptr,
                                                         const int32_t *col,
@@ -94,15 +100,23 @@ __global__ void __launch_bounds__(kApThreads) k_apply_T(int64_t n, const long lo
     T acc[G < 4 ? 4 : G];
 #pragma unroll
     for (int k = 0; k < (G < 4 ? 4 : G); ++k) acc[k] = T(0);
+    V csum = mk4<T>(0, 0, 0, 0);
     for (long long e = b + lane; e < e1; e += G) {
       const int i = __ldg(col + e);
       const long long ei = row_ptr[i] + tloc[e];
       const V c = ld4(coef + ei);
+      const V cs = ld4(coef + e);
+      csum.x += cs.x; csum.y += cs.y; csum.z += cs.z; csum.w += cs.w;
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
         const V g = ld4(gout + 4 * (int64_t)i + f);
         acc[f] += c.x * g.x + c.y * g.y + c.z * g.z + c.w * g.w;
       }
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const V g = ld4(gout + 4 * jr + f);
+      acc[f] -= csum.x * g.x + csum.y * g.y + csum.z * g.z + csum.w * g.w;
     }
     reduce_scatter<G, (G < 4 ? 4 : G)>(acc);
     T *o = reinterpret_cast<T *>(gfields + jr);
@@ -110,19 +124,47 @@ __global__ void __launch_bounds__(kApThreads) k_apply_T(int64_t n, const long lo
   }
 }
 
+template <typename T>
+static void launch_apply(mafp_ctx *ctx, cudaStream_t s, int64_t n, const long long *rp,
+                         const int32_t *col, const void *coef, const void *fields, void *out) {
+  using V = vec4_t<T>;
+  const int G = ctx->tune.apply_group;
+  const int blocks = grid_for(n * G, kApThreads, sm_count() * 64);
+  constexpr int U = sizeof(T) == 4 ? 4 : 2;
+  const V *c = (const V *)coef, *f = (const V *)fields;
+  T *o = (T *)out;
+  if (G == 4) {
+    MAFP_TIMED(ctx, s, "k_apply<G=4>", k_apply<T, 4, U><<<blocks, kApThreads, 0, s>>>(n, rp, col, c, f, o));
+  } else if (G == 16) {
+    MAFP_TIMED(ctx, s, "k_apply<G=16>", k_apply<T, 16, U><<<blocks, kApThreads, 0, s>>>(n, rp, col, c, f, o));
+  } else {
+    MAFP_TIMED(ctx, s, "k_apply<G=8>", k_apply<T, 8, U><<<blocks, kApThreads, 0, s>>>(n, rp, col, c, f, o));
+  }
+}
+
+template <typename T>
+static void launch_apply_T(mafp_ctx *ctx, cudaStream_t s, int64_t n, const long long *rp,
+                           const int32_t *col, const uint16_t *tloc, const void *coef,
+                           const void *gout, void *gfields) {
+  using V = vec4_t<T>;
+  const int G = ctx->tune.apply_group;
+  const int blocks = grid_for(n * G, kApThreads, sm_count() * 64);
+  const V *c = (const V *)coef, *g = (const V *)gout;
+  V *o = (V *)gfields;
+  if (G == 4) {
+    MAFP_TIMED(ctx, s, "k_apply_T<G=4>", k_apply_T<T, 4><<<blocks, kApThreads, 0, s>>>(n, rp, col, tloc, c, g, o));
+  } else if (G == 16) {
+    MAFP_TIMED(ctx, s, "k_apply_T<G=16>", k_apply_T<T, 16><<<blocks, kApThreads, 0, s>>>(n, rp, col, tloc, c, g, o));
+  } else {
+    MAFP_TIMED(ctx, s, "k_apply_T<G=8>", k_apply_T<T, 8><<<blocks, kApThreads, 0, s>>>(n, rp, col, tloc, c, g, o));
+  }
+}
+
 int apply_ops(mafp_ctx *ctx, int64_t n, int32_t dtype, const int64_t *row_ptr, const int32_t *col,
               const void *coef, const void *fields, void *out, cudaStream_t s) {
   const long long *rp = reinterpret_cast<const long long *>(row_ptr);
-  const int blocks = grid_for(n * 8, kApThreads, sm_count() * 64);
-  if (dtype == MAFP_F64) {
-    MAFP_TIMED(ctx, s, "k_apply<double,8,2>",
-               k_apply<double, 8, 2><<<blocks, kApThreads, 0, s>>>(n, rp, col, (const double4_16a *)coef,
-                                                        (const double4_16a *)fields, (double *)out));
-  } else {
-    MAFP_TIMED(ctx, s, "k_apply<float,8,4>",
-               k_apply<float, 8, 4><<<blocks, kApThreads, 0, s>>>(n, rp, col, (const float4 *)coef,
-                                                       (const float4 *)fields, (float *)out));
-  }
+  if (dtype == MAFP_F64) launch_apply<double>(ctx, s, n, rp, col, coef, fields, out);
+  else launch_apply<float>(ctx, s, n, rp, col, coef, fields, out);
   MAFP_LAUNCH_CHECK(ctx);
   return MAFP_OK;
 }
@@ -131,16 +173,8 @@ int apply_ops_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const int64_t *r
                        const int32_t *col, const uint16_t *tloc, const void *coef,
                        const void *gout, void *gfields, cudaStream_t s) {
   const long long *rp = reinterpret_cast<const long long *>(row_ptr);
-  const int blocks = grid_for(n * 8, kApThreads, sm_count() * 64);
-  if (dtype == MAFP_F64) {
-    MAFP_TIMED(ctx, s, "k_apply_T<double,8>",
-               k_apply_T<double, 8><<<blocks, kApThreads, 0, s>>>(n, rp, col, tloc, (const double4_16a *)coef,
-                                                       (const double4_16a *)gout, (double4_16a *)gfields));
-  } else {
-    MAFP_TIMED(ctx, s, "k_apply_T<float,8>",
-               k_apply_T<float, 8><<<blocks, kApThreads, 0, s>>>(n, rp, col, tloc, (const float4 *)coef,
-                                                      (const float4 *)gout, (float4 *)gfields));
-  }
+  if (dtype == MAFP_F64) launch_apply_T<double>(ctx, s, n, rp, col, tloc, coef, gout, gfields);
+  else launch_apply_T<float>(ctx, s, n, rp, col, tloc, coef, gout, gfields);
   MAFP_LAUNCH_CHECK(ctx);
   return MAFP_OK;
 }

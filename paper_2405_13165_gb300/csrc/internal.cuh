@@ -9,6 +9,8 @@
 namespace mafp {
 
 constexpr int kMaxRowSort = 2048;   // longest row the in-shared-memory row sort handles
+constexpr int kMaskCap = 1536;      // candidates of one cell tile in the neighbour mask kernel
+constexpr int kMaskWords = kMaskCap / 32;
 
 // Device status block (layout mirrored by mafp_status in the public header).
 struct DevStatus {
@@ -45,6 +47,7 @@ struct GridDev {
 
 struct mafp_ctx {
   mafp_params prm;
+  mafp_tuning tune;
   int64_t cap_particles;
   int64_t cap_cells;
   int device;
@@ -59,6 +62,8 @@ struct mafp_ctx {
   int32_t *ucell;           // [3 * cap] nonempty cells: key, start, end
   int32_t *n_ucell;         // device counter
   int32_t *counts;          // [cap] row lengths
+  uint32_t *nbr_mask;       // [kMaskWords * cap] candidate hit bits, word-major
+  int32_t *overflow;        // [cap] occupied cells whose candidates overflow the tile
   long long *scan_tmp;      // [cap/1024 + 2]
   double *bbox_partial;     // [1024 * 8]
   int32_t *fallback;        // [cap] particles re-done in FP64

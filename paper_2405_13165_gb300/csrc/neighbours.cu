@@ -52,15 +52,31 @@ __global__ void __launch_bounds__(kBoxThreads) k_bbox(const vec4_t<T> *pos, int6
   }
 }
 
-__global__ void k_grid(const double *partial, int nb, GridDev *g, DevStatus *st,
-                       long long cap_cells) {
-  if (threadIdx.x != 0) return;
+// One block of kBoxThreads threads reduces the per-block partials and sets the grid.
+__global__ void __launch_bounds__(kBoxThreads) k_grid(const double *partial, int nb, GridDev *g,
+                                                      DevStatus *st, long long cap_cells) {
   double v[8] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0, 0.0};
-  for (int b = 0; b < nb; ++b)
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
     for (int k = 0; k < 8; ++k) {
       double a = partial[b * 8 + k];
       v[k] = k < 3 ? fmin(v[k], a) : (k < 7 ? fmax(v[k], a) : v[k] + a);
     }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = fmin(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+#pragma unroll
+    for (int k = 3; k < 7; ++k) v[k] = fmax(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    v[7] += __shfl_xor_sync(0xffffffffu, v[7], o);
+  }
+  __shared__ double red[kBoxThreads / 32][8];
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < 8; ++k) red[threadIdx.x >> 5][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < kBoxThreads / 32; ++w)
+    for (int k = 0; k < 8; ++k)
+      v[k] = k < 3 ? fmin(v[k], red[w][k]) : (k < 7 ? fmax(v[k], red[w][k]) : v[k] + red[w][k]);
   g->ok = 0;
   if (v[7] > 0.0) {
     st->n_nonfinite += (long long)v[7];
@@ -127,7 +143,7 @@ __global__ void k_clear_cells(const GridDev *g, int32_t *cell_start, int32_t *ce
                               int32_t *n_ucell) {
   if (!g->ok) return;
   const long long nc = g->ncells;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *n_ucell = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) n_ucell[0] = n_ucell[1] = 0;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nc;
        k += (long long)gridDim.x * blockDim.x) {
     cell_start[k] = INT_MAX;
@@ -255,11 +271,15 @@ __device__ __forceinline__ bool in_support(const double4_16a &a, const double4_1
 constexpr int kNbrThreads = 128;
 constexpr int kNbrSmemBytes = 32768;
 
+// Warp-per-particle count / fill (ballot compaction), for the occupied cells
+// listed in sel[0 .. *n_sel): the cells whose 27-cell candidate union does not
+// fit the shared-memory tile of the mask kernel below.
 template <typename T, bool FILL>
 __global__ void __launch_bounds__(kNbrThreads) k_nbr(
-    const GridDev *g, const int32_t *ucell, const int32_t *n_ucell, const vec4_t<T> *spos,
-    const int32_t *svals, const int32_t *cell_start, const int32_t *cell_end, int32_t *counts,
-    const long long *row_ptr, int32_t *col, long long cap_nnz, int64_t n) {
+    const GridDev *g, const int32_t *ucell, const int32_t *sel, const int32_t *n_sel,
+    const vec4_t<T> *spos, const int32_t *svals, const int32_t *cell_start,
+    const int32_t *cell_end, int32_t *counts, const long long *row_ptr, int32_t *col,
+    long long cap_nnz, int64_t n) {
   using V = vec4_t<T>;
   constexpr int CAP = kNbrSmemBytes / sizeof(V);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -269,9 +289,10 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr(
   if (FILL && row_ptr[n] > cap_nnz) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = kNbrThreads / 32;
   const unsigned lt = (1u << lane) - 1u;
-  const int nu = *n_ucell;
+  const int nu = *n_sel;
   const int dx_ = g->dim[0], dy_ = g->dim[1], dz_ = g->dim[2];
-  for (int cb = blockIdx.x; cb < nu; cb += gridDim.x) {
+  for (int cs = blockIdx.x; cs < nu; cs += gridDim.x) {
+    const int cb = sel[cs];
     const int key = ucell[2 * cb], s0 = ucell[2 * cb + 1];
     const int s1 = cell_end[key];
     const int cx = key % dx_, cy = (key / dx_) % dy_, cz = key / (dx_ * dy_);
@@ -338,6 +359,190 @@ __global__ void k_check_nnz(const long long *row_ptr, int64_t n, long long cap_n
   st->nnz = nnz;
   if (nnz_dev) *nnz_dev = nnz;
   if (nnz > cap_nnz) set_error(st, MAFP_ECAPACITY, nnz);
+}
+
+// ------------------------------------------- thread-per-particle mask path
+// Every particle of a cell shares the candidate set "27 cells around it",
+// which is 9 runs of consecutive sorted positions (3 x-adjacent cells each).
+// The mask kernel stages that set in shared memory once per cell; each thread
+// (one particle) tests all candidates against itself reading them as shared
+// memory broadcasts, and writes one bit per candidate (word-major layout
+// mask[w * stride + p], coalesced across the block) plus its row length.
+// The expand kernel turns the bits back into column indices, so the distance
+// tests run once.
+constexpr int kMaskThreads = 64;
+constexpr int kExpThreads = 128;
+constexpr int kExpChunk = 64;             // particles of a cell expanded per round
+
+// Rows of the 27-cell neighbourhood of cell `key`: run r (dz = r/3-1,
+// dy = r%3-1) covers cells key-1..key+1 of that (y, z) row, clipped to the grid.
+__device__ __forceinline__ void cell_runs(int key, const GridDev *g, const int32_t *cell_start,
+                                          const int32_t *cell_end, int r, int *lo_out,
+                                          int *len_out) {
+  const int dx_ = g->dim[0], dy_ = g->dim[1], dz_ = g->dim[2];
+  const int cx = key % dx_, cy = (key / dx_) % dy_, cz = key / (dx_ * dy_);
+  const int ddz = r / 3 - 1, ddy = r % 3 - 1;
+  int lo = INT_MAX, hi = 0;
+  if (cz + ddz >= 0 && cz + ddz < dz_ && cy + ddy >= 0 && cy + ddy < dy_) {
+    const int base = key + ddz * dx_ * dy_ + ddy * dx_;
+    const int k0 = cx > 0 ? base - 1 : base, k1 = cx < dx_ - 1 ? base + 1 : base;
+    for (int k = k0; k <= k1; ++k) {
+      lo = min(lo, cell_start[k]);
+      hi = max(hi, cell_end[k]);
+    }
+  }
+  *lo_out = lo;
+  *len_out = hi > lo ? hi - lo : 0;
+}
+
+// FP32 test with an explicit band: certainly in / certainly out from FP32,
+// the FP64 definition inside +-1e-5 of the bound.
+__device__ __forceinline__ bool support_test(const float4 &a, const float4 &b) {
+  const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+  const float d2 = (dx * dx + dy * dy) + dz * dz;
+  const float r = (a.w + b.w) * 0.5f;
+  const float r2 = r * r;
+  if (d2 < r2 * 0.99999f) return true;
+  if (d2 > r2 * 1.00001f) return false;
+  return in_support64(a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w);
+}
+__device__ __forceinline__ bool support_test(const double4_16a &a, const double4_16a &b) {
+  return in_support64(a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
+    const GridDev *g, const int32_t *ucell, const int32_t *n_ucell, const vec4_t<T> *spos,
+    const int32_t *svals, const int32_t *cell_start, const int32_t *cell_end, int32_t *counts,
+    uint32_t *mask, int64_t stride, int32_t *overflow, int32_t *n_overflow) {
+  using V = vec4_t<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V *cand = reinterpret_cast<V *>(smem_raw);
+  __shared__ int r_lo[9], r_len[9], r_off[10];
+  if (!g->ok) return;
+  const int tid = threadIdx.x;
+  const int nu = *n_ucell;
+  for (int cb = blockIdx.x; cb < nu; cb += gridDim.x) {
+    const int key = ucell[2 * cb], s0 = ucell[2 * cb + 1];
+    const int s1 = cell_end[key];
+    if (tid < 9) cell_runs(key, g, cell_start, cell_end, tid, &r_lo[tid], &r_len[tid]);
+    __syncthreads();
+    if (tid == 0) {
+      int o = 0;
+      for (int r = 0; r < 9; ++r) {
+        r_off[r] = o;
+        o += r_len[r];
+      }
+      r_off[9] = o;
+      if (o > kMaskCap) overflow[atomicAdd(n_overflow, 1)] = cb;
+    }
+    __syncthreads();
+    const int total = r_off[9];
+    if (total <= kMaskCap) {
+      for (int r = 0; r < 9; ++r)
+        for (int t = tid; t < r_len[r]; t += kMaskThreads) cand[r_off[r] + t] = ld4(spos + r_lo[r] + t);
+      __syncthreads();
+      const int nwords = (total + 31) >> 5;
+      for (int p0 = s0; p0 < s1; p0 += kMaskThreads) {
+        const int p = p0 + tid;
+        const bool active = p < s1;
+        const V xi = ld4(spos + (active ? p : s0));
+        int cnt = 0;
+        for (int w = 0; w < nwords; ++w) {
+          const int base = w << 5;
+          const uint32_t valid = (total - base) >= 32 ? 0xffffffffu : ((1u << (total - base)) - 1u);
+          uint32_t m = 0, band = 0;
+          if constexpr (sizeof(T) == 4) {
+            // branch-free FP32 test of 32 candidates; the tile always holds
+            // 32 * nwords <= kMaskCap entries, so reads past `total` stay in it
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+              const float4 b = cand[base + k];
+              const float dx = b.x - xi.x, dy = b.y - xi.y, dz = b.z - xi.z;
+              const float d2 = (dx * dx + dy * dy) + dz * dz;
+              const float r = (xi.w + b.w) * 0.5f;
+              const float r2 = r * r;
+              m |= (d2 < r2 * 0.99999f ? 1u : 0u) << k;
+              band |= (d2 <= r2 * 1.00001f ? 1u : 0u) << k;
+            }
+            m &= valid;
+            band &= valid & ~m;
+            // pairs within 1e-5 of the bound: the FP64 definition decides
+            while (band) {
+              const int k = __ffs(band) - 1;
+              band &= band - 1;
+              const float4 b = cand[base + k];
+              if (in_support64(xi.x, xi.y, xi.z, xi.w, b.x, b.y, b.z, b.w)) m |= 1u << k;
+            }
+          } else {
+            for (int k = 0; k < 32; ++k)
+              if ((valid >> k) & 1u)
+                if (support_test(xi, cand[base + k])) m |= 1u << k;
+          }
+          if (active) mask[(int64_t)w * stride + p] = m;
+          cnt += __popc(m);
+        }
+        if (active) counts[svals[p]] = cnt;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kExpThreads) k_nbr_expand(
+    const GridDev *g, const int32_t *ucell, const int32_t *n_ucell, const int32_t *svals,
+    const int32_t *cell_start, const int32_t *cell_end, const uint32_t *mask, int64_t stride,
+    const long long *row_ptr, int32_t *col, long long cap_nnz, int64_t n) {
+  __shared__ int r_lo[9], r_len[9], r_off[10];
+  __shared__ uint32_t mw[kMaskWords][kExpChunk];
+  __shared__ int32_t cand_v[kMaskCap];   // original index of every candidate of the cell
+  if (!g->ok) return;
+  if (row_ptr[n] > cap_nnz) return;
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int nu = *n_ucell;
+  for (int cb = blockIdx.x; cb < nu; cb += gridDim.x) {
+    const int key = ucell[2 * cb], s0 = ucell[2 * cb + 1];
+    const int s1 = cell_end[key];
+    if (tid < 9) cell_runs(key, g, cell_start, cell_end, tid, &r_lo[tid], &r_len[tid]);
+    __syncthreads();
+    if (tid == 0) {
+      int o = 0;
+      for (int r = 0; r < 9; ++r) {
+        r_off[r] = o;
+        o += r_len[r];
+      }
+      r_off[9] = o;
+    }
+    __syncthreads();
+    const int total = r_off[9];
+    if (total <= kMaskCap) {
+      for (int r = 0; r < 9; ++r)
+        for (int t = tid; t < r_len[r]; t += kExpThreads) cand_v[r_off[r] + t] = svals[r_lo[r] + t];
+      const int nwords = (total + 31) >> 5;
+      for (int p0 = s0; p0 < s1; p0 += kExpChunk) {
+        const int np = min(kExpChunk, s1 - p0);
+        for (int k = tid; k < nwords * kExpChunk; k += kExpThreads) {
+          const int w = k / kExpChunk, q = k % kExpChunk;
+          mw[w][q] = q < np ? mask[(int64_t)w * stride + p0 + q] : 0u;
+        }
+        __syncthreads();
+        // one warp per particle, one candidate per lane: ballot compaction
+        for (int q = wp; q < np; q += kExpThreads / 32) {
+          long long at = row_ptr[svals[p0 + q]];
+          for (int w = 0; w < nwords; ++w) {
+            const uint32_t word = mw[w][q];
+            const bool hit = (word >> lane) & 1u;
+            if (hit) col[at + __popc(word & lt)] = cand_v[(w << 5) + lane];
+            at += __popc(word);
+          }
+        }
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // Rows come out ascending in cell order; when the input order differs from the
@@ -422,7 +627,7 @@ static int build_neighbours_t(mafp_ctx *ctx, int64_t n, const void *pos_h, int64
   MAFP_TIMED(ctx, s, "k_bbox<T>",
              k_bbox<T><<<nb_box, kBoxThreads, 0, s>>>(pos, n, ctx->bbox_partial));
   MAFP_TIMED(ctx, s, "k_grid",
-             k_grid<<<1, 32, 0, s>>>(ctx->bbox_partial, nb_box, ctx->d_grid, ctx->d_status, ctx->cap_cells));
+             k_grid<<<1, kBoxThreads, 0, s>>>(ctx->bbox_partial, nb_box, ctx->d_grid, ctx->d_status, ctx->cap_cells));
   MAFP_TIMED(ctx, s, "k_hash<T>",
              k_hash<T><<<grid_for(n, 256, sms * 16), 256, 0, s>>>(pos, n, ctx->d_grid, ctx->keys_a,
                                                        ctx->vals_a));
@@ -456,20 +661,31 @@ static int build_neighbours_t(mafp_ctx *ctx, int64_t n, const void *pos_h, int64
              k_identity_flag<<<1, 1, 0, s>>>(ctx->d_status));
   MAFP_LAUNCH_CHECK(ctx);
   const int nbr_blocks = sms * 8;
-  MAFP_TIMED(ctx, s, "k_nbr<T,false>",
+  int32_t *n_overflow = ctx->n_ucell + 1;
+  const int64_t stride = ctx->cap_particles;
+  MAFP_TIMED(ctx, s, sizeof(T) == 4 ? "k_nbr_mask<float>" : "k_nbr_mask<double>",
+             k_nbr_mask<T><<<sms * 16, kMaskThreads, kMaskCap * sizeof(V), s>>>(
+                 ctx->d_grid, ctx->ucell, ctx->n_ucell, spos, vin, ctx->cell_start,
+                 ctx->cell_end, ctx->counts, ctx->nbr_mask, stride, ctx->overflow, n_overflow));
+  MAFP_TIMED(ctx, s, "k_nbr<T,false>(overflow cells)",
              k_nbr<T, false><<<nbr_blocks, kNbrThreads, kNbrSmemBytes, s>>>(
-      ctx->d_grid, ctx->ucell, ctx->n_ucell, spos, vin, ctx->cell_start, ctx->cell_end,
-      ctx->counts, nullptr, nullptr, 0, n));
+      ctx->d_grid, ctx->ucell, ctx->overflow, n_overflow, spos, vin, ctx->cell_start,
+      ctx->cell_end, ctx->counts, nullptr, nullptr, 0, n));
   MAFP_LAUNCH_CHECK(ctx);
   int rc = scan_i32_to_i64(ctx, ctx->counts, reinterpret_cast<long long *>(row_ptr), n, s);
   if (rc) return rc;
   MAFP_TIMED(ctx, s, "k_check_nnz",
              k_check_nnz<<<1, 1, 0, s>>>(reinterpret_cast<const long long *>(row_ptr), n, cap_nnz, nnz_dev,
                               ctx->d_status, ctx->d_grid));
-  MAFP_TIMED(ctx, s, "k_nbr<T,true>",
+  MAFP_TIMED(ctx, s, "k_nbr_expand",
+             k_nbr_expand<T><<<sms * 16, kExpThreads, 0, s>>>(
+                 ctx->d_grid, ctx->ucell, ctx->n_ucell, vin, ctx->cell_start, ctx->cell_end,
+                 ctx->nbr_mask, stride, reinterpret_cast<const long long *>(row_ptr), col,
+                 cap_nnz, n));
+  MAFP_TIMED(ctx, s, "k_nbr<T,true>(overflow cells)",
              k_nbr<T, true><<<nbr_blocks, kNbrThreads, kNbrSmemBytes, s>>>(
-      ctx->d_grid, ctx->ucell, ctx->n_ucell, spos, vin, ctx->cell_start, ctx->cell_end,
-      ctx->counts, reinterpret_cast<const long long *>(row_ptr), col, cap_nnz, n));
+      ctx->d_grid, ctx->ucell, ctx->overflow, n_overflow, spos, vin, ctx->cell_start,
+      ctx->cell_end, ctx->counts, reinterpret_cast<const long long *>(row_ptr), col, cap_nnz, n));
   MAFP_TIMED(ctx, s, "k_rowsort",
              k_rowsort<<<grid_for(n, kSortWarps, sms * 8), kSortWarps * 32, 0, s>>>(
       reinterpret_cast<const long long *>(row_ptr), col, n, cap_nnz, ctx->d_status));
@@ -486,6 +702,10 @@ int build_neighbours(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h,
 }
 
 void init_kernel_attributes() {
+  cudaFuncSetAttribute(k_nbr_mask<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kMaskCap * (int)sizeof(float4));
+  cudaFuncSetAttribute(k_nbr_mask<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kMaskCap * (int)sizeof(double4_16a));
   cudaFuncSetAttribute(k_nbr<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kNbrSmemBytes);
   cudaFuncSetAttribute(k_nbr<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

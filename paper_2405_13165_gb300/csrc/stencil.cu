@@ -347,49 +347,61 @@ static StParams<C> make_params(const mafp_params &p, double piv_tol) {
   return sp;
 }
 
+template <typename TS, typename C, int M, int G, bool REFINE, bool QUEUE>
+static void launch_stencil(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void *pos_h,
+                           const uint8_t *model, const void *frame, const long long *rp,
+                           const int32_t *col, void *coef, uint8_t *status, float *cond,
+                           const StParams<C> &sp) {
+  using V = vec4_t<TS>;
+  static char name[96];
+  snprintf(name, sizeof(name), "k_stencil<%s,M=%d,G=%d,%s>", sizeof(TS) == 4 ? "f32" : "f64",
+           M, G, REFINE ? "refined" : "plain");
+  const int blocks = grid_for(n * G, kStThreads, sm_count() * 64);
+  MAFP_TIMED(ctx, s, name,
+             k_stencil<TS, C, M, G, REFINE, QUEUE><<<blocks, kStThreads, 0, s>>>(
+                 n, (const V *)pos_h, model, (const V *)frame, rp, col, (V *)coef, status, cond,
+                 sp, ctx->d_status, ctx->fallback));
+}
+
+// Group size G chosen at run time (tuning), instantiated for 8/16/32 (3D) and 4/8/16 (2D).
+template <typename TS, typename C, bool REFINE, bool QUEUE>
+static int dispatch_stencils(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void *pos_h,
+                             const uint8_t *model, const void *frame, const long long *rp,
+                             const int32_t *col, void *coef, uint8_t *status, float *cond,
+                             const StParams<C> &sp) {
+  switch (ctx->tune.stencil3d_group) {
+    case 8: launch_stencil<TS, C, 10, 8, REFINE, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, coef, status, cond, sp); break;
+    case 16: launch_stencil<TS, C, 10, 16, REFINE, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, coef, status, cond, sp); break;
+    default: launch_stencil<TS, C, 10, 32, REFINE, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, coef, status, cond, sp); break;
+  }
+  switch (ctx->tune.stencil2d_group) {
+    case 4: launch_stencil<TS, C, 6, 4, REFINE, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, coef, status, cond, sp); break;
+    case 16: launch_stencil<TS, C, 6, 16, REFINE, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, coef, status, cond, sp); break;
+    default: launch_stencil<TS, C, 6, 8, REFINE, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, coef, status, cond, sp); break;
+  }
+  MAFP_LAUNCH_CHECK(ctx);
+  return MAFP_OK;
+}
+
 int build_stencils(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h,
                    const uint8_t *model, const void *frame, const int64_t *row_ptr,
                    const int32_t *col, void *coef, uint8_t *status, float *cond, cudaStream_t s) {
   const long long *rp = reinterpret_cast<const long long *>(row_ptr);
   const int sms = sm_count();
-  const int b3 = grid_for(n * 32, kStThreads, sms * 64);
-  const int b2 = grid_for(n * 8, kStThreads, sms * 64);
   if (dtype == MAFP_F64) {
     const StParams<double> sp = make_params<double>(ctx->prm, 1e-12);
-    MAFP_TIMED(ctx, s, "k_stencil<double,double,10,32,false,false>",
-               k_stencil<double, double, 10, 32, false, false><<<b3, kStThreads, 0, s>>>(
-        n, (const double4_16a *)pos_h, model, (const double4_16a *)frame, rp, col, (double4_16a *)coef,
-        status, cond, sp, ctx->d_status, ctx->fallback));
-    MAFP_TIMED(ctx, s, "k_stencil<double,double,6,8,false,false>",
-               k_stencil<double, double, 6, 8, false, false><<<b2, kStThreads, 0, s>>>(
-        n, (const double4_16a *)pos_h, model, (const double4_16a *)frame, rp, col, (double4_16a *)coef,
-        status, cond, sp, ctx->d_status, ctx->fallback));
-    MAFP_LAUNCH_CHECK(ctx);
-    return MAFP_OK;
+    return dispatch_stencils<double, double, false, false>(ctx, s, n, pos_h, model, frame, rp,
+                                                          col, coef, status, cond, sp);
   }
   const StParams<float> sp = make_params<float>(ctx->prm, 1e-6);
   const StParams<double> sp64 = make_params<double>(ctx->prm, 1e-12);
-  MAFP_TIMED(ctx, s, "k_reset_queue",
-             k_reset_queue<<<1, 1, 0, s>>>(ctx->d_status));
-  if (dtype == MAFP_F32_PLAIN) {
-    MAFP_TIMED(ctx, s, "k_stencil<float,float,10,32,false,true>",
-               k_stencil<float, float, 10, 32, false, true><<<b3, kStThreads, 0, s>>>(
-        n, (const float4 *)pos_h, model, (const float4 *)frame, rp, col, (float4 *)coef, status,
-        cond, sp, ctx->d_status, ctx->fallback));
-    MAFP_TIMED(ctx, s, "k_stencil<float,float,6,8,false,true>",
-               k_stencil<float, float, 6, 8, false, true><<<b2, kStThreads, 0, s>>>(
-        n, (const float4 *)pos_h, model, (const float4 *)frame, rp, col, (float4 *)coef, status,
-        cond, sp, ctx->d_status, ctx->fallback));
-  } else {
-    MAFP_TIMED(ctx, s, "k_stencil<float,float,10,32,true,true>",
-               k_stencil<float, float, 10, 32, true, true><<<b3, kStThreads, 0, s>>>(
-        n, (const float4 *)pos_h, model, (const float4 *)frame, rp, col, (float4 *)coef, status,
-        cond, sp, ctx->d_status, ctx->fallback));
-    MAFP_TIMED(ctx, s, "k_stencil<float,float,6,8,true,true>",
-               k_stencil<float, float, 6, 8, true, true><<<b2, kStThreads, 0, s>>>(
-        n, (const float4 *)pos_h, model, (const float4 *)frame, rp, col, (float4 *)coef, status,
-        cond, sp, ctx->d_status, ctx->fallback));
-  }
+  MAFP_TIMED(ctx, s, "k_reset_queue", k_reset_queue<<<1, 1, 0, s>>>(ctx->d_status));
+  int rc = dtype == MAFP_F32_PLAIN
+               ? dispatch_stencils<float, float, false, true>(ctx, s, n, pos_h, model, frame, rp,
+                                                             col, coef, status, cond, sp)
+               : dispatch_stencils<float, float, true, true>(ctx, s, n, pos_h, model, frame, rp,
+                                                            col, coef, status, cond, sp);
+  if (rc) return rc;
   MAFP_TIMED(ctx, s, "k_stencil_redo<10,32>",
              k_stencil_redo<10, 32><<<sms * 4, kStThreads, 0, s>>>(
       (const float4 *)pos_h, model, (const float4 *)frame, rp, col, (float4 *)coef, status, cond,

@@ -43,6 +43,11 @@ class Status(C.Structure):
                 ("n_nonfinite", C.c_int64), ("ncells", C.c_int64), ("cell_size", C.c_double)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("stencil3d_group", C.c_int32), ("stencil2d_group", C.c_int32),
+                ("apply_group", C.c_int32), ("reserved", C.c_int32)]
+
+
 class KernelTime(C.Structure):
     _fields_ = [("name", C.c_char * 64), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -84,9 +89,11 @@ def lib():
         L.mafp_apply_ops_backward.argtypes = [p, i64, i32, p, p, p, p, p, p, p]
         L.mafp_build_stencils_backward.argtypes = [p, i64, i32, p, p, p, p, p, p, p, p, p]
         L.mafp_remap_switched.argtypes = [p, i64, i32, p, p, p, p, p, i64, p, p, p]
+        L.mafp_set_tuning.argtypes = [p, p]
+        L.mafp_get_tuning.argtypes = [p, p]
         L.mafp_profile.argtypes = [p, i32]
         L.mafp_profile_read.argtypes = [p, p, i32, p]
-        for name in ("mafp_profile", "mafp_profile_read", "mafp_create", "mafp_destroy", "mafp_get_status", "mafp_reset_status",
+        for name in ("mafp_set_tuning", "mafp_get_tuning", "mafp_profile", "mafp_profile_read", "mafp_create", "mafp_destroy", "mafp_get_status", "mafp_reset_status",
                      "mafp_build_neighbours", "mafp_classify_pca", "mafp_build_stencils",
                      "mafp_apply_ops", "mafp_transpose_map", "mafp_apply_ops_backward",
                      "mafp_build_stencils_backward", "mafp_remap_switched"):
@@ -167,6 +174,17 @@ class Context:
         st = Status()
         self.check(lib().mafp_get_status(self.handle, C.byref(st), _stream(stream)))
         return {k: getattr(st, k) for k, _ in Status._fields_}
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        self.check(lib().mafp_get_tuning(self.handle, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_ if k != "reserved"}
+
+    def set_tuning(self, **kw):
+        cur = self.tuning()
+        cur.update(kw)
+        t = Tuning(**cur)
+        self.check(lib().mafp_set_tuning(self.handle, C.byref(t)))
 
     def profile(self, enable: bool):
         """Start (clearing the record) or stop kernel-level event timing."""

@@ -22,7 +22,7 @@ def cloud_to_device(cloud, dtype=M.F32_REFINED, device="cuda", pin=False):
         if t.dtype in (torch.float32, torch.float64):
             t = t.to(rd)
         out[k] = t.to(device, non_blocking=False)
-    out["vol"] = (out["mass"].to(torch.float64) / out["rho"].to(torch.float64)).to(rd)
+    out["vol"] = torch.from_numpy(np.ascontiguousarray(cloud.vol)).to(rd).to(device)
     out["fields"] = out["vp"]
     return out
 

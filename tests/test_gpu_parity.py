@@ -113,17 +113,20 @@ def test_boundary_band_pairs_fp32(orc):
     # path retakes them in FP64 and must agree with the oracle's definition
     rng = np.random.default_rng(7)
     pts = []
-    for k in range(400):
+    for k in range(512):
         h = rng.uniform(0.05, 0.2)
         d = rng.normal(size=3)
         d /= np.linalg.norm(d)
-        base = rng.uniform(0, 1, 3)
-        r = np.float32(h) * np.float32(1.0 + rng.integers(-3, 4) * 6e-8)
+        # pairs on a lattice of spacing 0.6 > max support radius, so pairs are separate
+        base = np.array([k % 8, (k // 8) % 8, k // 64]) * 0.6 + rng.uniform(0, 0.1, 3)
+        r = h * (1.0 + rng.integers(-3, 4) * 6e-8)
         pts.append([*base, h])
         pts.append([*(base + d * r), h])
-    P = np.array(pts).astype(np.float32).astype(np.float64)
-    P[:, :3] += np.repeat(np.arange(400)[:, None] * 3.0, 2, 0)   # separate the pairs
+    P = np.array(pts).astype(np.float32).astype(np.float64)   # both sides see these values
     rp, col = orc.neighbours(P)
+    near = [k for k in range(0, len(P), 2)
+            if abs(np.sum((P[k, :3] - P[k + 1, :3]) ** 2) / (P[k, 3] ** 2) - 1) < 1e-5]
+    assert len(near) > 100      # most pairs sit inside the FP64 retake band
     ctx = M.Context(P.shape[0])
     g_rp, g_col, _ = M.neighbours(ctx, torch.tensor(P, dtype=torch.float32, device="cuda"))
     np.testing.assert_array_equal(g_rp.cpu().numpy(), rp)
@@ -185,3 +188,16 @@ def test_apply_transpose(orc, dtype):
     want = orc.apply_T(o["row_ptr"], o["col"], o["coef"], G)
     scale = np.abs(want).max(0)
     assert np.all(np.abs(got - want).max(0) <= TOL[dtype] * scale)
+
+
+@pytest.mark.parametrize("g3,g2,ga", [(8, 4, 4), (16, 16, 16), (32, 8, 8)])
+def test_launch_shapes_agree_with_oracle(orc, g3, g2, ga):
+    c = C.config_small()
+    o = _oracle_all(orc, c)
+    ctx = M.Context(c.n)
+    ctx.set_tuning(stencil3d_group=g3, stencil2d_group=g2, apply_group=ga)
+    g, *_ = run_gpu(c, M.F32_REFINED, ctx=ctx)
+    err, _ = stencil_rowwise_error_vec(o["row_ptr"], g["coef"], o["coef"])
+    assert np.all(err <= TOL[M.F32_REFINED]), err
+    nw, p99 = column_error(g["out"], o["out"])
+    assert np.all(nw <= TOL[M.F32_REFINED]), (nw, p99)
