@@ -13,6 +13,12 @@ namespace mafp {
 constexpr int kClsThreads = 128;
 constexpr int kClsGroup = 8;
 
+// Thresholds prepared on the host so the FP32 path compares in FP32 only.
+struct ClsConst {
+  double cth;  // cos(theta*)
+  float cth_f, eps_max_f, eps_band_f, angle_band_f, hfilm_band_f;
+};
+
 // One pass over the row of particle i: number of same-model neighbours and
 // the sum of their coordinates q = (x_j - x_i)/h_i (for the centroid of
 // Sec. 4.1.2); for a 2D particle also Eq. Height over its 2D neighbours
@@ -116,12 +122,12 @@ __global__ void __launch_bounds__(kClsThreads) k_classify(
     int64_t n, const vec4_t<T> *pos, const uint8_t *model, const uint8_t *type,
     const vec4_t<T> *normal, const T *vol, const T *h3d, const uint8_t *user,
     const long long *row_ptr, const int32_t *col, uint8_t *preflag, vec4_t<T> *eig,
-    vec4_t<T> *frame, T *hfilm, uint8_t *near, mafp_params prm, DevStatus *st) {
+    vec4_t<T> *frame, T *hfilm, uint8_t *near, mafp_params prm, ClsConst kc, DevStatus *st) {
   using V = vec4_t<T>;
   const int lane = threadIdx.x & (G - 1);
   const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
-  const double cth = cos(prm.theta_star);
+  const double cth = kc.cth;
   for (int64_t i = gid; i < n; i += ngroups) {
     const uint8_t mi = model[i], ti = type[i], ui = user[i];
     uint8_t pre = 0, nr = 0;
@@ -156,10 +162,14 @@ __global__ void __launch_bounds__(kClsThreads) k_classify(
           const T ndw = fabs(nv.x * W[2][0] + nv.y * W[2][1] + nv.z * W[2][2]);
           bool certain = true;
           if constexpr (sizeof(T) == 4) {
-            const bool eps_unsure = fabsf(eps - (float)prm.eps_lambda_max) <= (float)prm.eps_band;
-            const bool eps_pass = eps < (float)prm.eps_lambda_max;
-            const bool ang_unsure = fabsf(ndw - (float)cth) <= (float)prm.angle_band || gap < 1e-2f;
+            const bool eps_unsure = fabsf(eps - kc.eps_max_f) <= kc.eps_band_f;
+            const bool eps_pass = eps < kc.eps_max_f;
+            const bool ang_unsure = fabsf(ndw - kc.cth_f) <= kc.angle_band_f || gap < 1e-2f;
             certain = !(eps_unsure || (eps_pass && ang_unsure));
+            if (certain) {
+              // FP32 decision away from both thresholds
+              pre = ((eps_pass && ndw >= kc.cth_f) || (ui & MAFP_USER_TO_2D)) ? 1 : 0;
+            }
           }
           double e64 = eps, d64 = ndw;
           if (!certain) {
@@ -175,8 +185,10 @@ __global__ void __launch_bounds__(kClsThreads) k_classify(
             }
             eps = (T)e64;
           }
-          const bool pass = (e64 < prm.eps_lambda_max) && (d64 >= cth);
-          pre = (pass || (ui & MAFP_USER_TO_2D)) ? 1 : 0;
+          if (sizeof(T) == 8 || !certain) {
+            const bool pass = (e64 < prm.eps_lambda_max) && (d64 >= cth);
+            pre = (pass || (ui & MAFP_USER_TO_2D)) ? 1 : 0;
+          }
           if ((sizeof(T) == 8 || retake) && !(ui & MAFP_USER_TO_2D)) {
             const bool en = fabs(e64 - prm.eps_lambda_max) <= prm.near_rel * prm.eps_lambda_max;
             const bool an = fabs(d64 - cth) <= prm.near_rel;
@@ -193,18 +205,22 @@ __global__ void __launch_bounds__(kClsThreads) k_classify(
       } else {
         // Eq. 2Dto3Dcond
         const T hd = h3d[i];
-        double H64 = H;
         bool certain = true;
-        if constexpr (sizeof(T) == 4) certain = fabsf(H - hd) > (float)prm.hfilm_band * hd;
-        if (!certain) {
-          retake = true;
-          H64 = hfilm64<G>(i, pos, model, type, vol, row_ptr, col, prm.alpha_film);
-          H = (T)H64;
+        if constexpr (sizeof(T) == 4) {
+          certain = fabsf(H - hd) > kc.hfilm_band_f * hd;
+          if (certain) pre = (H >= hd || (ui & MAFP_USER_TO_3D)) ? 2 : 0;
         }
-        pre = (H64 >= (double)hd || (ui & MAFP_USER_TO_3D)) ? 2 : 0;
-        if ((sizeof(T) == 8 || retake) && !(ui & MAFP_USER_TO_3D) &&
-            fabs(H64 - (double)hd) <= prm.near_rel * (double)hd)
-          nr = 1;
+        if (sizeof(T) == 8 || !certain) {
+          double H64 = H;
+          if (!certain) {
+            retake = true;
+            H64 = hfilm64<G>(i, pos, model, type, vol, row_ptr, col, prm.alpha_film);
+            H = (T)H64;
+          }
+          pre = (H64 >= (double)hd || (ui & MAFP_USER_TO_3D)) ? 2 : 0;
+          if (!(ui & MAFP_USER_TO_3D) && fabs(H64 - (double)hd) <= prm.near_rel * (double)hd)
+            nr = 1;
+        }
       }
     }
     if (lane == 0) {
@@ -253,6 +269,13 @@ int classify_pca(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h, con
                  void *hfilm, uint8_t *near, cudaStream_t s) {
   constexpr int G = kClsGroup;
   const int blocks = grid_for(n * G, kClsThreads, sm_count() * 32);
+  ClsConst kc;
+  kc.cth = cos(ctx->prm.theta_star);
+  kc.cth_f = (float)kc.cth;
+  kc.eps_max_f = (float)ctx->prm.eps_lambda_max;
+  kc.eps_band_f = (float)ctx->prm.eps_band;
+  kc.angle_band_f = (float)ctx->prm.angle_band;
+  kc.hfilm_band_f = (float)ctx->prm.hfilm_band;
   const long long *rp = reinterpret_cast<const long long *>(row_ptr);
   if (dtype == MAFP_F64) {
     MAFP_TIMED(ctx, s, "k_classify<double>",
@@ -260,13 +283,13 @@ int classify_pca(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h, con
                    n, (const double4_16a *)pos_h, model, type, (const double4_16a *)normal,
                    (const double *)vol, (const double *)h3d, user, rp, col, preflag,
                    (double4_16a *)eig, (double4_16a *)frame, (double *)hfilm, near, ctx->prm,
-                   ctx->d_status));
+                   kc, ctx->d_status));
   } else {
     MAFP_TIMED(ctx, s, "k_classify<float>",
                k_classify<float, G><<<blocks, kClsThreads, 0, s>>>(
                    n, (const float4 *)pos_h, model, type, (const float4 *)normal,
                    (const float *)vol, (const float *)h3d, user, rp, col, preflag, (float4 *)eig,
-                   (float4 *)frame, (float *)hfilm, near, ctx->prm, ctx->d_status));
+                   (float4 *)frame, (float *)hfilm, near, ctx->prm, kc, ctx->d_status));
   }
   MAFP_TIMED(ctx, s, "k_smooth",
              k_smooth<G><<<blocks, kClsThreads, 0, s>>>(n, model, preflag, last, rp, col, flag));

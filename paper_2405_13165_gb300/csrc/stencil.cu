@@ -121,6 +121,36 @@ __device__ __forceinline__ void chol_solve(const C (&L)[Basis<M>::NA], const C (
   }
 }
 
+// Same solve with the factor read from shared memory (every lane of the group
+// reads the same address: a broadcast), which keeps the 55 entries of L out
+// of the registers during the refinement pass.
+template <int M, typename C>
+__device__ __forceinline__ void chol_solve_s(const C *L, const C (&invd)[M], const C (&b)[M],
+                                             C (&x)[M]) {
+  C y[M];
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+    C s = b[r];
+#pragma unroll
+    for (int l = 0; l < r; ++l) s -= L[pk(r, l)] * y[l];
+    y[r] = s * invd[r];
+  }
+#pragma unroll
+  for (int r = M - 1; r >= 0; --r) {
+    C s = y[r];
+#pragma unroll
+    for (int l = r + 1; l < M; ++l) s -= L[pk(l, r)] * x[l];
+    x[r] = s * invd[r];
+  }
+}
+
+template <int M, int G>
+struct StSmem {
+  static constexpr int NA = Basis<M>::NA, NR = Basis<M>::NR;
+  static constexpr int SCR = pad_to(NA, G) > pad_to(NR * M, G) ? pad_to(NA, G) : pad_to(NR * M, G);
+  static constexpr int PER_GROUP = SCR + NA;   // reduce scratch + Cholesky factor
+};
+
 // Process particle i with a group of G lanes.  Returns (through *result)
 //  0 = written, 1 = deficient (zeros written), 2 = queued for FP64.
 template <typename TS, typename C, int M, int G, bool REFINE, bool QUEUE>
@@ -181,6 +211,12 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
   C invd[M], pmin, pmax;
   const bool ok = (cnt >= M) && cholesky<M, C>(L, invd, sp.piv_tol_rel * tr, pmin, pmax);
   const C cond = (pmax / pmin) * (pmax / pmin);
+  C *Ls = sm + StSmem<M, G>::SCR;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NA; ++k) Ls[k] = L[k];
+  }
+  __syncwarp(gm);
   if (!ok || (QUEUE && !(cond <= sp.cond_max))) {
     // deficient (decided in this precision unless queued) -> zeros
     if (QUEUE && cnt >= M) {
@@ -199,7 +235,7 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
     C bb[M];
 #pragma unroll
     for (int r = 0; r < M; ++r) bb[r] = rhs<M, C>(k, r);
-    chol_solve<M, C>(L, invd, bb, lam[k]);
+    chol_solve_s<M, C>(Ls, invd, bb, lam[k]);
   }
   if constexpr (REFINE) {
     // residual b - sum_j c_j p_j of the coefficients as they will be stored
@@ -230,7 +266,7 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
       C rr[M], d[M];
 #pragma unroll
       for (int r = 0; r < M; ++r) rr[r] = rhs<M, C>(k, r) - sm[k * M + r];
-      chol_solve<M, C>(L, invd, rr, d);
+      chol_solve_s<M, C>(Ls, invd, rr, d);
 #pragma unroll
       for (int r = 0; r < M; ++r) lam[k][r] += d[r];
     }
@@ -269,12 +305,12 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
 
 // Main kernel: every particle of model (M == 10 ? 3D : 2D).
 template <typename TS, typename C, int M, int G, bool REFINE, bool QUEUE>
-__global__ void __launch_bounds__(kStThreads) k_stencil(
+__global__ void __launch_bounds__(kStThreads, 4) k_stencil(
     int64_t n, const vec4_t<TS> *pos, const uint8_t *model, const vec4_t<TS> *frame,
     const long long *row_ptr, const int32_t *col, vec4_t<TS> *coef, uint8_t *status,
     float *cond, StParams<C> sp, DevStatus *st, int32_t *queue) {
   constexpr int NA = Basis<M>::NA, NR = Basis<M>::NR;
-  constexpr int SMG = pad_to(NA, G) > pad_to(NR * M, G) ? pad_to(NA, G) : pad_to(NR * M, G);
+  constexpr int SMG = StSmem<M, G>::PER_GROUP;
   __shared__ C smem[(kStThreads / G) * SMG];
   const int grp = threadIdx.x / G;
   C *sm = smem + grp * SMG;
@@ -308,7 +344,7 @@ __global__ void __launch_bounds__(kStThreads) k_stencil_redo(
     const int32_t *col, float4 *coef, uint8_t *status, float *cond, StParams<double> sp,
     DevStatus *st, const int32_t *queue) {
   constexpr int NA = Basis<M>::NA, NR = Basis<M>::NR;
-  constexpr int SMG = pad_to(NA, G) > pad_to(NR * M, G) ? pad_to(NA, G) : pad_to(NR * M, G);
+  constexpr int SMG = StSmem<M, G>::PER_GROUP;
   __shared__ double smem[(kStThreads / G) * SMG];
   const int grp = threadIdx.x / G;
   double *sm = smem + grp * SMG;
