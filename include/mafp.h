@@ -183,6 +183,31 @@ int mafp_build_stencils(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos
                         void *stream);
 
 /* --------------------------------------------------------------------------
+ * mafp_build_stencils_noalloc -- mafp_build_stencils without a context and
+ * without allocating (the paper has no counterpart: this serves callers).
+ * Some callers cannot call cudaMalloc: a plug-in inside a host application
+ * that owns the whole device-memory budget through its own pool, or a time
+ * step that must not stall on the implicit device synchronisation of
+ * cudaMalloc / cudaFree.  This entry point takes the same arrays as
+ * mafp_build_stencils (plus the parameters, NULL = defaults) and uses, as its
+ * only scratch, a fixed array compiled into the library: the FP64-retake queue
+ * for up to MAFP_NOALLOC_MAX_PARTICLES particles plus a few counters, about
+ * 4 MB, present on every GPU that loads the library until the process exits.
+ *  - n > MAFP_NOALLOC_MAX_PARTICLES returns MAFP_ECAPACITY and enqueues nothing.
+ *  - The first call on a device looks up the array's device address on the
+ *    current device (cudaGetSymbolAddress); make that first call before any
+ *    stream capture.  A failed lookup returns MAFP_ECUDA.
+ *  - Every call shares the one array and resets the queue length itself, so
+ *    calls whose work overlaps on the GPU (different streams, or host threads
+ *    without ordering) race on it: serialise them.
+ *  - Launch shapes are the defaults; device-side counters are not reported. */
+#define MAFP_NOALLOC_MAX_PARTICLES (1 << 20)
+int mafp_build_stencils_noalloc(int64_t n, int32_t dtype, const mafp_params *params,
+                                const void *pos_h, const uint8_t *model, const void *frame,
+                                const int64_t *row_ptr, const int32_t *col, void *coef,
+                                uint8_t *status, float *cond, void *stream);
+
+/* --------------------------------------------------------------------------
  * mafp_apply_ops -- stencil application, Eq. GFDM_Definition:
  *   out[i][f] = sum_{e in row i} coef[e] * (fields[col[e]][f] - fields[i][f]),
  *   f = u, v, w, p.  The coefficients must annihilate constants
