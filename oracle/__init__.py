@@ -75,6 +75,7 @@ def lib():
         L.orc_apply.argtypes = [i64, p, p, p, p, p, i64, p]
         L.orc_apply_T.argtypes = [i64, p, p, p, p, p]
         L.orc_remap.argtypes = [i64, p, p, p, p, p, p, i64, p]
+        L.orc_stencil_grad.argtypes = [i64, p, p, p, p, p, p, p, p]
         L.orc_remap.restype = i64
         _lib = L
     return _lib
@@ -230,6 +231,21 @@ def apply_T(row_ptr, col, coef, gout):
     lib().orc_apply_T(n, _ptr(row_ptr), _ptr(np.ascontiguousarray(col, np.int32)), _ptr(cf),
                       _ptr(np.ascontiguousarray(G)), _ptr(gf))
     return gf
+
+
+def stencil_grad(pos_h, model, row_ptr, col, fields, gout, prm=None):
+    """dL/dx [n,4] through the stencils, given gout = dL/dout [n,4,4]."""
+    P = _f64(pos_h, 4)
+    n = P.shape[0]
+    F = _f64(fields, 4)
+    G = np.ascontiguousarray(_f64(gout).reshape(n, 4, 4))
+    g = np.zeros((n, 4))
+    pr = _params(prm)
+    lib().orc_stencil_grad(n, _ptr(P), _ptr(_u8(model)),
+                           _ptr(np.ascontiguousarray(row_ptr, np.int64)),
+                           _ptr(np.ascontiguousarray(col, np.int32)), C.byref(pr), _ptr(F),
+                           _ptr(G), _ptr(g))
+    return g
 
 
 def _state_arrays(st: dict, n: int):

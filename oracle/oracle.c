@@ -531,6 +531,148 @@ void orc_stencils(int64_t n, const double *P, const uint8_t *model, const int64_
   }
 }
 
+/* ---------------------------------------------------------------------------
+ * Adjoint of the stencils with respect to the positions (differentiation of
+ * out_i = sum_j c_ij (u_j - u_i), Eq. GFDM_Definition, with the stencils of
+ * stencil_one).  For one row, with gbar_jk = dL/dc_jk:
+ *   lambda_k = A^-1 b_k,  lbar_k = sum_j gbar_jk w_j p_j,  mu_k = A^-1 lbar_k,
+ *   s_jk = p_j.lambda_k,  t_jk = p_j.mu_k,
+ *   wbar_j = sum_k (gbar_jk - t_jk) s_jk,
+ *   pbar_j = w_j sum_k (gbar_jk lambda_k - s_jk mu_k - t_jk lambda_k),
+ * then through p(q) and w(|q|) to q_j = (x_j - x_i)/h_i.  Neighbour sets,
+ * models and (for film rows) the tangent frame are held fixed.
+ * ------------------------------------------------------------------------- */
+static double weight_dw_over_s(double s, double alpha) {
+  /* W'(s)/s for s <= 1 (W of weight_w), 0 outside the support */
+  if (s > 1.0) return 0.0;
+  return -2.0 * alpha * exp(-alpha * s * s) / (1.0 - exp(-alpha));
+}
+
+static void stencil_grad_one(int64_t i, const double *P, const uint8_t *model,
+                             const int64_t *row_ptr, const int32_t *col, const orc_params *prm,
+                             const double *fields, const double *gout, double *gpos) {
+  const int is2d = model[i] == M2D;
+  const int m = is2d ? 6 : 10, nr = is2d ? 3 : 4;
+  const double h = P[4 * i + 3];
+  double t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0};
+  if (is2d) {
+    double lam[3], V[9];
+    orc_pca(P, model, row_ptr, col, i, lam, V);
+    for (int a = 0; a < 3; ++a) { t1[a] = V[a * 3 + 0]; t2[a] = V[a * 3 + 1]; }
+  }
+  double A[100] = {0}, p[10];
+  int64_t cnt = 0;
+  for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+    int64_t j = col[e];
+    if (model[j] != model[i]) continue;
+    double d[3], q[3];
+    for (int a = 0; a < 3; ++a) d[a] = P[4 * j + a] - P[4 * i + a];
+    double w = weight_w(sqrt(dist2(P, i, j)) / h, prm->alpha_w);
+    if (is2d) {
+      basis2((d[0] * t1[0] + d[1] * t1[1] + d[2] * t1[2]) / h,
+             (d[0] * t2[0] + d[1] * t2[1] + d[2] * t2[2]) / h, p);
+    } else {
+      for (int a = 0; a < 3; ++a) q[a] = d[a] / h;
+      basis3(q, p);
+    }
+    for (int r = 0; r < m; ++r)
+      for (int c = 0; c < m; ++c) A[r * m + c] += w * p[r] * p[c];
+    ++cnt;
+  }
+  double tr = 0.0;
+  for (int r = 0; r < m; ++r) tr += A[r * m + r];
+  double pmin, pmax;
+  if (cnt < m || cholesky(m, A, 1e-12 * tr, &pmin, &pmax)) return; /* zero stencil, no gradient */
+  double b[4][10] = {{0}}, lam[4][10], lbar[4][10] = {{0}}, mu[4][10];
+  if (is2d) {
+    b[0][1] = 1.0 / h; b[1][2] = 1.0 / h;
+    b[2][3] = 2.0 / (h * h); b[2][5] = 2.0 / (h * h);
+  } else {
+    b[0][1] = 1.0 / h; b[1][2] = 1.0 / h; b[2][3] = 1.0 / h;
+    b[3][4] = 2.0 / (h * h); b[3][5] = 2.0 / (h * h); b[3][6] = 2.0 / (h * h);
+  }
+  for (int k = 0; k < nr; ++k) chol_solve(m, A, b[k], lam[k]);
+  /* dL/dc for the row: gbar_jk = sum_f gout[i][f][op] (u_j - u_i); for a film row
+   * the gradient outputs are c^xi t1 + c^eta t2, so gbar^xi = gbar . t1, etc. */
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      int64_t j = col[e];
+      if (model[j] != model[i]) continue;
+      double g4[4];
+      for (int op = 0; op < 4; ++op) {
+        double s = 0.0;
+        for (int f = 0; f < 4; ++f) s += gout[16 * i + 4 * f + op] * (fields[4 * j + f] - fields[4 * i + f]);
+        g4[op] = s;
+      }
+      double gb[4];
+      if (is2d) {
+        gb[0] = g4[0] * t1[0] + g4[1] * t1[1] + g4[2] * t1[2];
+        gb[1] = g4[0] * t2[0] + g4[1] * t2[1] + g4[2] * t2[2];
+        gb[2] = g4[3];
+      } else {
+        for (int k = 0; k < 4; ++k) gb[k] = g4[k];
+      }
+      double d[3], q[3];
+      for (int a = 0; a < 3; ++a) d[a] = P[4 * j + a] - P[4 * i + a];
+      double s_ = sqrt(dist2(P, i, j)) / h;
+      double w = weight_w(s_, prm->alpha_w);
+      double xi = 0, eta = 0;
+      if (is2d) {
+        xi = (d[0] * t1[0] + d[1] * t1[1] + d[2] * t1[2]) / h;
+        eta = (d[0] * t2[0] + d[1] * t2[1] + d[2] * t2[2]) / h;
+        basis2(xi, eta, p);
+      } else {
+        for (int a = 0; a < 3; ++a) q[a] = d[a] / h;
+        basis3(q, p);
+      }
+      if (pass == 0) {
+        for (int k = 0; k < nr; ++k)
+          for (int r = 0; r < m; ++r) lbar[k][r] += gb[k] * w * p[r];
+        continue;
+      }
+      double sk[4], tk[4], wbar = 0.0, pbar[10] = {0};
+      for (int k = 0; k < nr; ++k) {
+        sk[k] = 0.0;
+        tk[k] = 0.0;
+        for (int r = 0; r < m; ++r) {
+          sk[k] += p[r] * lam[k][r];
+          tk[k] += p[r] * mu[k][r];
+        }
+        wbar += (gb[k] - tk[k]) * sk[k];
+        for (int r = 0; r < m; ++r)
+          pbar[r] += w * (gb[k] * lam[k][r] - sk[k] * mu[k][r] - tk[k] * lam[k][r]);
+      }
+      double dbar[3];
+      double wq = weight_dw_over_s(s_, prm->alpha_w) * wbar; /* dW/dq = W'(s) q / s */
+      if (is2d) {
+        double xib = pbar[1] + 2.0 * xi * pbar[3] + eta * pbar[4];
+        double etb = pbar[2] + xi * pbar[4] + 2.0 * eta * pbar[5];
+        for (int a = 0; a < 3; ++a) dbar[a] = (xib * t1[a] + etb * t2[a]) / h + wq * d[a] / (h * h);
+      } else {
+        double qb[3];
+        qb[0] = pbar[1] + 2.0 * q[0] * pbar[4] + q[1] * pbar[7] + q[2] * pbar[8];
+        qb[1] = pbar[2] + 2.0 * q[1] * pbar[5] + q[0] * pbar[7] + q[2] * pbar[9];
+        qb[2] = pbar[3] + 2.0 * q[2] * pbar[6] + q[0] * pbar[8] + q[1] * pbar[9];
+        for (int a = 0; a < 3; ++a) dbar[a] = (qb[a] + wq * q[a]) / h;
+      }
+      for (int a = 0; a < 3; ++a) {
+        gpos[4 * j + a] += dbar[a];
+        gpos[4 * i + a] -= dbar[a];
+      }
+    }
+    if (pass == 0)
+      for (int k = 0; k < nr; ++k) chol_solve(m, A, lbar[k], mu[k]);
+  }
+}
+
+void orc_stencil_grad(int64_t n, const double *P, const uint8_t *model, const int64_t *row_ptr,
+                      const int32_t *col, const orc_params *prm, const double *fields,
+                      const double *gout, double *gpos) {
+  for (int64_t k = 0; k < 4 * n; ++k) gpos[k] = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    stencil_grad_one(i, P, model, row_ptr, col, prm, fields, gout, gpos);
+}
+
 /* Eq. GFDM_Definition: d*_i u = sum_{j in S_i} c*_ij u_j, for the four fields. */
 void orc_apply(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *coef,
                const double *fields, const int64_t *rows, int64_t nrows, double *out) {

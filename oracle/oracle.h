@@ -80,6 +80,14 @@ void orc_stencils(int64_t n, const double *P, const uint8_t *model, const int64_
                   const int32_t *col, const orc_params *prm, const int64_t *rows,
                   int64_t nrows, double *coef, uint8_t *status, double *cond);
 
+/* Gradient of a loss L(out) with respect to the positions x (gpos [n][4],
+ * h component 0) through the stencils of orc_stencils, given
+ * gout = dL/dout [n][4][4] and the fields; out_i = sum_j c_ij (u_j - u_i).
+ * Neighbour sets, models and film tangent frames are held fixed. */
+void orc_stencil_grad(int64_t n, const double *P, const uint8_t *model, const int64_t *row_ptr,
+                      const int32_t *col, const orc_params *prm, const double *fields,
+                      const double *gout, double *gpos);
+
 /* Stencil application of Eq. GFDM_Definition: out[i][f] = (d_x, d_y, d_z, Lap)
  * of field f at particle i, fields f = 0..3. */
 void orc_apply(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *coef,

@@ -1,0 +1,87 @@
+"""Pins of the oracle's position gradient through the GFDM stencils against
+central finite differences in FP64 (neighbour sets held fixed)."""
+import numpy as np
+import pytest
+
+from paper_2405_13165_gb300 import clouds as C
+
+
+def _loss(orc, P, model, rp, col, F, G):
+    coef, status, _ = orc.stencils(P, model, rp, col)
+    out = orc.apply(rp, col, coef, F)
+    return float(np.sum(out * G)), out
+
+
+def _safe_coords(P, rp, col, i, step):
+    """Coordinate i is usable when no pair involving it sits within 10 steps
+    of the support boundary (W' jumps there)."""
+    r = col[rp[i]:rp[i + 1]]
+    d = np.linalg.norm(P[r, :3] - P[i, :3], axis=1)
+    return np.all(np.abs(d - P[i, 3]) > 10 * step)
+
+
+@pytest.mark.parametrize("loss", ["laplacian", "random"])
+def test_gradient_matches_central_differences(orc, loss):
+    c = C.cube_on_sheet(0.05, cube=0.4, sheet=1.0)   # 512 + 384 particles
+    P = c.pos_h.astype(np.float64)
+    F = c.vp.astype(np.float64)
+    rp, col = orc.neighbours(P)
+    rng = np.random.default_rng(1)
+    coef, status, _ = orc.stencils(P, c.model, rp, col)
+    out = orc.apply(rp, col, coef, F)
+    if loss == "laplacian":
+        # L = sum_i sum_f (Lap_i f)^2  ->  dL/dout = 2 Lap on the Laplacian channel
+        G = np.zeros_like(out)
+        G[:, :, 3] = 2.0 * out[:, :, 3]
+    else:
+        G = rng.normal(size=out.shape)
+    g = orc.stencil_grad(P, c.model, rp, col, F, G)
+    dx = 0.05
+    step = 1e-4 * dx
+    picks = rng.choice(c.n, 60, replace=False)
+    checked = 0
+    for i in picks:
+        if not _safe_coords(P, rp, col, i, step):
+            continue
+        # film rows hold their tangent frame fixed: the out-of-plane coordinate of
+        # a film particle is checked only for the Laplacian loss (first-order exact)
+        axes = (0, 1, 2) if (c.model[i] == 0 or loss == "laplacian") else (0, 1)
+        for a in axes:
+            Pp = P.copy()
+            Pm = P.copy()
+            Pp[i, a] += step
+            Pm[i, a] -= step
+            if loss == "laplacian":
+                lp = np.sum(_loss(orc, Pp, c.model, rp, col, F, G)[1][:, :, 3] ** 2)
+                lm = np.sum(_loss(orc, Pm, c.model, rp, col, F, G)[1][:, :, 3] ** 2)
+            else:
+                lp = _loss(orc, Pp, c.model, rp, col, F, G)[0]
+                lm = _loss(orc, Pm, c.model, rp, col, F, G)[0]
+            fd = (lp - lm) / (2 * step)
+            scale = max(abs(fd), 1e-3 * np.abs(g[:, :3]).max())
+            assert abs(g[i, a] - fd) <= 2e-5 * scale + 1e-9, (i, a, g[i, a], fd)
+            checked += 1
+    assert checked >= 60
+    assert np.all(g[:, 3] == 0.0)
+
+
+def test_gradient_of_translation_invariant_loss_sums_to_zero(orc):
+    # stencils depend on differences x_j - x_i only, so translating every
+    # particle changes nothing: the gradient summed over particles vanishes
+    c = C.cube_on_sheet(0.05, cube=0.4, sheet=1.0)
+    P = c.pos_h.astype(np.float64)
+    rp, col = orc.neighbours(P)
+    rng = np.random.default_rng(2)
+    G = rng.normal(size=(c.n, 4, 4))
+    # fields moving with the particles (u_j - u_i fixed): only the stencils change
+    g = orc.stencil_grad(P, c.model, rp, col, c.vp.astype(np.float64), G)
+    tot = g[:, :3].sum(0)
+    assert np.all(np.abs(tot) <= 1e-9 * np.abs(g[:, :3]).sum(0))
+
+
+def test_gradient_zero_for_deficient_rows(orc):
+    P = np.array([[0, 0, 0, 1.0], [0.2, 0, 0, 1.0], [0, 0.2, 0, 1.0], [0, 0, 0.2, 1.0]])
+    rp, col = orc.neighbours(P)
+    g = orc.stencil_grad(P, np.zeros(4, np.uint8), rp, col, np.ones((4, 4)),
+                         np.ones((4, 4, 4)))
+    assert np.all(g == 0)
