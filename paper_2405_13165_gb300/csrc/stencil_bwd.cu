@@ -1,14 +1,308 @@
-// stencil_bwd.cu -- adjoint of the GFDM stencil build with respect to the
-// particle positions (recomputing moments and factors per particle).
+// stencil_bwd.cu -- adjoint of (build_stencils, apply_ops) with respect to the
+// particle positions, recomputing the moment matrix and its Cholesky factor
+// per particle (no stored factors).
+//
+// For one row i with c_jk = w_j p_j . lambda_k, (sum_j w_j p_j p_j^T) lambda_k = b_k
+// and gbar_jk = dL/dc_jk = sum_f gout[i][f][k] (u_j - u_i):
+//   lbar_k = sum_j gbar_jk w_j p_j,  mu_k = A^-1 lbar_k,
+//   s_jk = p_j . lambda_k,  t_jk = p_j . mu_k,
+//   wbar_j = sum_k (gbar_jk - t_jk) s_jk,
+//   pbar_j = w_j sum_k (gbar_jk lambda_k - s_jk mu_k - t_jk lambda_k),
+// then through p(q) and W(|q|) to q_j = (x_j - x_i)/h_i, scattered to x_j and
+// x_i (atomic adds).  Film rows use the tangent frame of `frame` held fixed.
+// The unscaled right-hand sides of the forward kernel are used; the 1/h and
+// 1/h^2 output factors are folded into gbar.
 #include "internal.cuh"
+#include "stencil_common.cuh"
 
 namespace mafp {
 
-int build_stencils_backward(mafp_ctx *ctx, int64_t, int32_t, const void *, const uint8_t *,
-                            const void *, const int64_t *, const int32_t *, const void *,
-                            const void *, void *, cudaStream_t) {
-  snprintf(ctx->err, sizeof(ctx->err), "mafp_build_stencils_backward: not built yet");
-  return MAFP_ENOTIMPL;
+template <typename T> __device__ __forceinline__ void atomic_add_r(T *p, T v) { atomicAdd(p, v); }
+
+// Returns 0 done, 1 no gradient (deficient), 2 queued for the FP64 redo.
+template <typename TS, typename C, int M, int G, bool QUEUE>
+__device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *model,
+                             const vec4_t<TS> *frame, const long long *row_ptr,
+                             const int32_t *col, const vec4_t<TS> *fields,
+                             const vec4_t<TS> *gout, TS *gpos, const StParams<C> &sp, C *sm) {
+  constexpr int NA = Basis<M>::NA, NR = Basis<M>::NR;
+  constexpr int VA = pad_to(NA, G), VR = pad_to(NR * M, G);
+  using V = vec4_t<TS>;
+  const int lane = threadIdx.x & (G - 1);
+  const unsigned gm = group_mask<G>();
+  const V xi = ld4(pos + i);
+  const uint8_t mi = model[i];
+  const C hinv = C(1) / C(xi.w);
+  C t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0};
+  if constexpr (M == 6) {
+    const V f1 = ld4(frame + 2 * i), f3 = ld4(frame + 2 * i + 1);
+    t1[0] = C(f1.x); t1[1] = C(f1.y); t1[2] = C(f1.z);
+    const C n0 = C(f3.x), n1 = C(f3.y), n2 = C(f3.z);
+    t2[0] = n1 * t1[2] - n2 * t1[1];
+    t2[1] = n2 * t1[0] - n0 * t1[2];
+    t2[2] = n0 * t1[1] - n1 * t1[0];
+  }
+  const long long b = row_ptr[i], e1 = row_ptr[i + 1];
+  // ---- moments and factor (as in the forward build)
+  C A[VA];
+#pragma unroll
+  for (int k = 0; k < VA; ++k) A[k] = C(0);
+  int cnt = 0;
+  for (long long e = b + lane; e < e1; e += G) {
+    const int j = col[e];
+    if (model[j] != mi) continue;
+    C p[M];
+    const C w = basis_at<M, C>(xi, ld4(pos + j), hinv, t1, t2, sp, p);
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+      const C wp = w * p[r];
+#pragma unroll
+      for (int c = 0; c <= r; ++c) A[pk(r, c)] += wp * p[c];
+    }
+    ++cnt;
+  }
+  cnt = group_sum<G>(cnt);
+  reduce_scatter<G, VA>(A);
+  __syncwarp(gm);
+#pragma unroll
+  for (int k = 0; k < VA / G; ++k) sm[lane * (VA / G) + k] = A[k];
+  __syncwarp(gm);
+  C L[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) L[k] = sm[k];
+  __syncwarp(gm);
+  C tr = 0;
+#pragma unroll
+  for (int r = 0; r < M; ++r) tr += L[pk(r, r)];
+  C invd[M], pmin, pmax;
+  const bool ok = (cnt >= M) && cholesky<M, C>(L, invd, sp.piv_tol_rel * tr, pmin, pmax);
+  const C cond = (pmax / pmin) * (pmax / pmin);
+  if (!ok || (QUEUE && !(cond <= sp.cond_max))) return (QUEUE && cnt >= M) ? 2 : 1;
+  C *Ls = sm + StSmem<M, G>::SCR;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NA; ++k) Ls[k] = L[k];
+  }
+  __syncwarp(gm);
+  C lam[NR][M];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    C bb[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) bb[r] = rhs<M, C>(k, r);
+    chol_solve_s<M, C>(Ls, invd, bb, lam[k]);
+  }
+  // per-operator output scale of the forward kernel: gradient 1/h, Laplacian 1/h^2
+  const C h2inv = hinv * hinv;
+  const V fi = ld4(fields + i);
+  V go[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) go[f] = ld4(gout + 4 * i + f);
+  // gbar (scaled) of one neighbour, in the basis' operator order
+  auto gbar = [&](const V &fj, C (&gb)[NR]) {
+    const C du[4] = {C(fj.x) - C(fi.x), C(fj.y) - C(fi.y), C(fj.z) - C(fi.z), C(fj.w) - C(fi.w)};
+    C g4[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      g4[0] += C(go[f].x) * du[f];
+      g4[1] += C(go[f].y) * du[f];
+      g4[2] += C(go[f].z) * du[f];
+      g4[3] += C(go[f].w) * du[f];
+    }
+    if constexpr (M == 10) {
+      gb[0] = g4[0] * hinv; gb[1] = g4[1] * hinv; gb[2] = g4[2] * hinv; gb[3] = g4[3] * h2inv;
+    } else {
+      gb[0] = (g4[0] * t1[0] + g4[1] * t1[1] + g4[2] * t1[2]) * hinv;
+      gb[1] = (g4[0] * t2[0] + g4[1] * t2[1] + g4[2] * t2[2]) * hinv;
+      gb[2] = g4[3] * h2inv;
+    }
+  };
+  // ---- pass 1: lbar_k = sum_j gbar_jk w_j p_j, then mu_k = A^-1 lbar_k
+  {
+    C R[VR];
+#pragma unroll
+    for (int k = 0; k < VR; ++k) R[k] = C(0);
+    for (long long e = b + lane; e < e1; e += G) {
+      const int j = col[e];
+      if (model[j] != mi) continue;
+      C p[M], gb[NR];
+      const C w = basis_at<M, C>(xi, ld4(pos + j), hinv, t1, t2, sp, p);
+      gbar(ld4(fields + j), gb);
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        const C gw = gb[k] * w;
+#pragma unroll
+        for (int r = 0; r < M; ++r) R[k * M + r] += gw * p[r];
+      }
+    }
+    reduce_scatter<G, VR>(R);
+#pragma unroll
+    for (int k = 0; k < VR / G; ++k) sm[lane * (VR / G) + k] = R[k];
+    __syncwarp(gm);
+  }
+  C mu[NR][M];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    C lb[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) lb[r] = sm[k * M + r];
+    chol_solve_s<M, C>(Ls, invd, lb, mu[k]);
+  }
+  __syncwarp(gm);
+  // ---- pass 2: wbar, pbar -> dL/dx_j (scattered) and -sum for x_i
+  const C a2 = C(-2) * sp.alpha * sp.inv_den;  // W'(s)/s = a2 exp(-alpha s^2)
+  C acc_i[3] = {0, 0, 0};
+  for (long long e = b + lane; e < e1; e += G) {
+    const int j = col[e];
+    if (model[j] != mi || j == i) continue;
+    const V xj = ld4(pos + j);
+    C p[M], gb[NR];
+    const C w = basis_at<M, C>(xi, xj, hinv, t1, t2, sp, p);
+    gbar(ld4(fields + j), gb);
+    const C dx = C(xj.x) - C(xi.x), dy = C(xj.y) - C(xi.y), dz = C(xj.z) - C(xi.z);
+    const C s2 = ((dx * dx + dy * dy) + dz * dz) * (hinv * hinv);
+    const C dws = s2 <= C(1) ? a2 * exp(-sp.alpha * s2) : C(0);
+    C wbar = 0, pbar[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) pbar[r] = 0;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      C s = 0, t = 0;
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        s += p[r] * lam[k][r];
+        t += p[r] * mu[k][r];
+      }
+      wbar += (gb[k] - t) * s;
+#pragma unroll
+      for (int r = 0; r < M; ++r) pbar[r] += w * (gb[k] * lam[k][r] - s * mu[k][r] - t * lam[k][r]);
+    }
+    const C wq = dws * wbar;
+    C d[3];
+    if constexpr (M == 10) {
+      const C qx = dx * hinv, qy = dy * hinv, qz = dz * hinv;
+      const C gx = pbar[1] + C(2) * qx * pbar[4] + qy * pbar[7] + qz * pbar[8];
+      const C gy = pbar[2] + C(2) * qy * pbar[5] + qx * pbar[7] + qz * pbar[9];
+      const C gz = pbar[3] + C(2) * qz * pbar[6] + qx * pbar[8] + qy * pbar[9];
+      d[0] = (gx + wq * qx) * hinv;
+      d[1] = (gy + wq * qy) * hinv;
+      d[2] = (gz + wq * qz) * hinv;
+    } else {
+      const C xi_ = p[1], et_ = p[2];
+      const C xb = pbar[1] + C(2) * xi_ * pbar[3] + et_ * pbar[4];
+      const C eb = pbar[2] + xi_ * pbar[4] + C(2) * et_ * pbar[5];
+      d[0] = (xb * t1[0] + eb * t2[0]) * hinv + wq * dx * hinv * hinv;
+      d[1] = (xb * t1[1] + eb * t2[1]) * hinv + wq * dy * hinv * hinv;
+      d[2] = (xb * t1[2] + eb * t2[2]) * hinv + wq * dz * hinv * hinv;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      atomic_add_r<TS>(gpos + 4 * (int64_t)j + a, TS(d[a]));
+      acc_i[a] -= d[a];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) acc_i[a] = group_sum<G>(acc_i[a]);
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) atomic_add_r<TS>(gpos + 4 * i + a, TS(acc_i[a]));
+  }
+  return 0;
+}
+
+template <typename TS, typename C, int M, int G, bool QUEUE>
+__global__ void __launch_bounds__(kStThreads) k_stencil_grad(
+    int64_t n, const vec4_t<TS> *pos, const uint8_t *model, const vec4_t<TS> *frame,
+    const long long *row_ptr, const int32_t *col, const vec4_t<TS> *fields,
+    const vec4_t<TS> *gout, TS *gpos, StParams<C> sp, DevStatus *st, int32_t *queue) {
+  constexpr int SMG = StSmem<M, G>::PER_GROUP;
+  __shared__ C smem[(kStThreads / G) * SMG];
+  C *sm = smem + (threadIdx.x / G) * SMG;
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const uint8_t want = M == 10 ? MAFP_MODEL_3D : MAFP_MODEL_2D;
+  for (int64_t i = gid; i < n; i += ngroups) {
+    if (model[i] != want) continue;
+    const int res = grad_particle<TS, C, M, G, QUEUE>(i, pos, model, frame, row_ptr, col, fields,
+                                                     gout, gpos, sp, sm);
+    if (res == 2 && lane == 0) queue[atomicAdd(&st->fallback_count, 1)] = (int32_t)i;
+  }
+}
+
+// FP64 redo of the queued rows of one model (FP32 storage).
+template <int M, int G>
+__global__ void __launch_bounds__(kStThreads) k_stencil_grad_redo(
+    const float4 *pos, const uint8_t *model, const float4 *frame, const long long *row_ptr,
+    const int32_t *col, const float4 *fields, const float4 *gout, float *gpos,
+    StParams<double> sp, const DevStatus *st, const int32_t *queue) {
+  constexpr int SMG = StSmem<M, G>::PER_GROUP;
+  __shared__ double smem[(kStThreads / G) * SMG];
+  double *sm = smem + (threadIdx.x / G) * SMG;
+  const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int nq = st->fallback_count;
+  const uint8_t want = M == 10 ? MAFP_MODEL_3D : MAFP_MODEL_2D;
+  for (int64_t q = gid; q < nq; q += ngroups) {
+    const int64_t i = queue[q];
+    if (model[i] != want) continue;
+    grad_particle<float, double, M, G, false>(i, pos, model, frame, row_ptr, col, fields, gout,
+                                              gpos, sp, sm);
+  }
+}
+
+__global__ void k_reset_grad_queue(DevStatus *st) { st->fallback_count = 0; }
+
+template <typename TS, typename C, bool QUEUE>
+static void launch_grad(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void *pos_h,
+                        const uint8_t *model, const void *frame, const long long *rp,
+                        const int32_t *col, const void *fields, const void *gout, void *gpos,
+                        const StParams<C> &sp) {
+  using V = vec4_t<TS>;
+  const int sms = sm_count();
+  constexpr int G3 = 16, G2 = 8;
+  MAFP_TIMED(ctx, s, sizeof(TS) == 4 ? "k_stencil_grad<f32,M=10>" : "k_stencil_grad<f64,M=10>",
+             (k_stencil_grad<TS, C, 10, G3, QUEUE><<<grid_for(n * G3, kStThreads, sms * 64),
+                                                    kStThreads, 0, s>>>(
+                 n, (const V *)pos_h, model, (const V *)frame, rp, col, (const V *)fields,
+                 (const V *)gout, (TS *)gpos, sp, ctx->d_status, ctx->fallback)));
+  MAFP_TIMED(ctx, s, sizeof(TS) == 4 ? "k_stencil_grad<f32,M=6>" : "k_stencil_grad<f64,M=6>",
+             (k_stencil_grad<TS, C, 6, G2, QUEUE><<<grid_for(n * G2, kStThreads, sms * 64),
+                                                   kStThreads, 0, s>>>(
+                 n, (const V *)pos_h, model, (const V *)frame, rp, col, (const V *)fields,
+                 (const V *)gout, (TS *)gpos, sp, ctx->d_status, ctx->fallback)));
+}
+
+int build_stencils_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h,
+                            const uint8_t *model, const void *frame, const int64_t *row_ptr,
+                            const int32_t *col, const void *fields, const void *gout, void *gpos,
+                            cudaStream_t s) {
+  const long long *rp = reinterpret_cast<const long long *>(row_ptr);
+  const size_t real = dtype == MAFP_F64 ? sizeof(double) : sizeof(float);
+  MAFP_CUDA_TRY(ctx, cudaMemsetAsync(gpos, 0, (size_t)n * 4 * real, s));
+  if (dtype == MAFP_F64) {
+    launch_grad<double, double, false>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout,
+                                       gpos, make_params<double>(ctx->prm, 1e-12));
+    MAFP_LAUNCH_CHECK(ctx);
+    return MAFP_OK;
+  }
+  MAFP_TIMED(ctx, s, "k_reset_grad_queue", k_reset_grad_queue<<<1, 1, 0, s>>>(ctx->d_status));
+  launch_grad<float, float, true>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos,
+                                  make_params<float>(ctx->prm, 1e-6));
+  const StParams<double> sp64 = make_params<double>(ctx->prm, 1e-12);
+  const int sms = sm_count();
+  MAFP_TIMED(ctx, s, "k_stencil_grad_redo<10>",
+             (k_stencil_grad_redo<10, 32><<<sms * 4, kStThreads, 0, s>>>(
+                 (const float4 *)pos_h, model, (const float4 *)frame, rp, col,
+                 (const float4 *)fields, (const float4 *)gout, (float *)gpos, sp64,
+                 ctx->d_status, ctx->fallback)));
+  MAFP_TIMED(ctx, s, "k_stencil_grad_redo<6>",
+             (k_stencil_grad_redo<6, 8><<<sms * 4, kStThreads, 0, s>>>(
+                 (const float4 *)pos_h, model, (const float4 *)frame, rp, col,
+                 (const float4 *)fields, (const float4 *)gout, (float *)gpos, sp64,
+                 ctx->d_status, ctx->fallback)));
+  MAFP_LAUNCH_CHECK(ctx);
+  return MAFP_OK;
 }
 
 }  // namespace mafp

@@ -1,0 +1,163 @@
+// stencil_common.cuh -- device pieces shared by the GFDM stencil build and its
+// adjoint: monomial bases, the least-squares weight, packed Cholesky and solves.
+#pragma once
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace mafp {
+
+constexpr int kStThreads = 128;
+
+template <int M> struct Basis;
+template <> struct Basis<10> {
+  static constexpr int NA = 55;   // packed lower triangle of A
+  static constexpr int NR = 4;    // right-hand sides: d/dx, d/dy, d/dz, Laplacian
+};
+template <> struct Basis<6> {
+  static constexpr int NA = 21;
+  static constexpr int NR = 3;    // d/dxi, d/deta, surface Laplacian
+};
+
+__host__ __device__ constexpr int pad_to(int v, int g) { return ((v + g - 1) / g) * g; }
+__host__ __device__ constexpr int pk(int r, int c) { return r * (r + 1) / 2 + c; }
+
+template <typename C>
+struct StParams {
+  C alpha, ea, inv_den;   // W(s) = (exp(-alpha s^2) - ea) * inv_den, s <= 1
+  C piv_tol_rel;          // pivot <= tol * trace -> rank deficient (FP64) / fall back (FP32)
+  C cond_max;
+};
+
+template <typename C>
+__device__ __forceinline__ C weight_w(C s2, const StParams<C> &sp) {
+  return s2 <= C(1) ? (exp(-sp.alpha * s2) - sp.ea) * sp.inv_den : C(0);
+}
+
+// Monomial basis at one neighbour; returns w (0 for j outside the unit support).
+template <int M, typename C, typename V>
+__device__ __forceinline__ C basis_at(const V &xi, const V &xj, C hinv, const C (&t1)[3],
+                                      const C (&t2)[3], const StParams<C> &sp, C (&p)[M]) {
+  const C dx = C(xj.x) - C(xi.x), dy = C(xj.y) - C(xi.y), dz = C(xj.z) - C(xi.z);
+  const C s2 = ((dx * dx + dy * dy) + dz * dz) * (hinv * hinv);
+  const C w = weight_w<C>(s2, sp);
+  if constexpr (M == 10) {
+    const C qx = dx * hinv, qy = dy * hinv, qz = dz * hinv;
+    p[0] = C(1); p[1] = qx; p[2] = qy; p[3] = qz;
+    p[4] = qx * qx; p[5] = qy * qy; p[6] = qz * qz;
+    p[7] = qx * qy; p[8] = qx * qz; p[9] = qy * qz;
+  } else {
+    const C xi_ = (dx * t1[0] + dy * t1[1] + dz * t1[2]) * hinv;
+    const C et_ = (dx * t2[0] + dy * t2[1] + dz * t2[2]) * hinv;
+    p[0] = C(1); p[1] = xi_; p[2] = et_;
+    p[3] = xi_ * xi_; p[4] = xi_ * et_; p[5] = et_ * et_;
+  }
+  return w;
+}
+
+// Right-hand side k (unscaled: the 1/h and 1/h^2 factors are applied to the output).
+template <int M, typename C>
+__device__ __forceinline__ C rhs(int k, int r) {
+  if constexpr (M == 10) {
+    if (k < 3) return r == k + 1 ? C(1) : C(0);
+    return (r >= 4 && r <= 6) ? C(2) : C(0);
+  } else {
+    if (k < 2) return r == k + 1 ? C(1) : C(0);
+    return (r == 3 || r == 5) ? C(2) : C(0);
+  }
+}
+
+// In-register Cholesky of the packed matrix L (lower), returns false when a
+// pivot is <= tol.  invd gets 1/L_kk; pmin / pmax the extreme pivots.
+template <int M, typename C>
+__device__ __forceinline__ bool cholesky(C (&L)[Basis<M>::NA], C (&invd)[M], C tol, C &pmin,
+                                         C &pmax) {
+  pmin = C(INFINITY);
+  pmax = C(0);
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    C d = L[pk(k, k)];
+#pragma unroll
+    for (int l = 0; l < k; ++l) d -= L[pk(k, l)] * L[pk(k, l)];
+    ok = ok && (d > tol);
+    const C lkk = sqrt(d > tol ? d : C(1));
+    L[pk(k, k)] = lkk;
+    invd[k] = C(1) / lkk;
+    pmin = lkk < pmin ? lkk : pmin;
+    pmax = lkk > pmax ? lkk : pmax;
+#pragma unroll
+    for (int r = k + 1; r < M; ++r) {
+      C s = L[pk(r, k)];
+#pragma unroll
+      for (int l = 0; l < k; ++l) s -= L[pk(r, l)] * L[pk(k, l)];
+      L[pk(r, k)] = s * invd[k];
+    }
+  }
+  return ok;
+}
+
+template <int M, typename C>
+__device__ __forceinline__ void chol_solve(const C (&L)[Basis<M>::NA], const C (&invd)[M],
+                                           const C (&b)[M], C (&x)[M]) {
+  C y[M];
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+    C s = b[r];
+#pragma unroll
+    for (int l = 0; l < r; ++l) s -= L[pk(r, l)] * y[l];
+    y[r] = s * invd[r];
+  }
+#pragma unroll
+  for (int r = M - 1; r >= 0; --r) {
+    C s = y[r];
+#pragma unroll
+    for (int l = r + 1; l < M; ++l) s -= L[pk(l, r)] * x[l];
+    x[r] = s * invd[r];
+  }
+}
+
+// Same solve with the factor read from shared memory (every lane of the group
+// reads the same address: a broadcast), which keeps the 55 entries of L out
+// of the registers during the refinement pass.
+template <int M, typename C>
+__device__ __forceinline__ void chol_solve_s(const C *L, const C (&invd)[M], const C (&b)[M],
+                                             C (&x)[M]) {
+  C y[M];
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+    C s = b[r];
+#pragma unroll
+    for (int l = 0; l < r; ++l) s -= L[pk(r, l)] * y[l];
+    y[r] = s * invd[r];
+  }
+#pragma unroll
+  for (int r = M - 1; r >= 0; --r) {
+    C s = y[r];
+#pragma unroll
+    for (int l = r + 1; l < M; ++l) s -= L[pk(l, r)] * x[l];
+    x[r] = s * invd[r];
+  }
+}
+
+template <int M, int G>
+struct StSmem {
+  static constexpr int NA = Basis<M>::NA, NR = Basis<M>::NR;
+  static constexpr int SCR = pad_to(NA, G) > pad_to(NR * M, G) ? pad_to(NA, G) : pad_to(NR * M, G);
+  static constexpr int PER_GROUP = SCR + NA;   // reduce scratch + Cholesky factor
+};
+
+
+template <typename C>
+inline StParams<C> make_params(const mafp_params &p, double piv_tol) {
+  StParams<C> sp;
+  const double ea = exp(-p.alpha_w);
+  sp.alpha = (C)p.alpha_w;
+  sp.ea = (C)ea;
+  sp.inv_den = (C)(1.0 / (1.0 - ea));
+  sp.piv_tol_rel = (C)piv_tol;
+  sp.cond_max = (C)p.cond_fp64;
+  return sp;
+}
+
+}  // namespace mafp

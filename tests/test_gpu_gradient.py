@@ -1,0 +1,83 @@
+"""GPU gradients through the C ABI: the transpose of apply_ops (fields) and the
+stencil adjoint (positions), against the FP64 oracle gradient (itself pinned by
+central finite differences) and, in FP64, against torch's own finite-difference
+gradcheck of the GPU forward."""
+import numpy as np
+import pytest
+
+from paper_2405_13165_gb300 import clouds as C
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+from paper_2405_13165_gb300 import mafp as M  # noqa: E402
+from paper_2405_13165_gb300.autograd import gfdm_operators  # noqa: E402
+from parity_util import run_gpu  # noqa: E402
+
+
+def _setup(c, dtype):
+    g, pipe, d, ctx = run_gpu(c, dtype, stages=("nbr", "cls"))
+    n = c.n
+    rp, col = pipe.csr(n)
+    return ctx, d, rp, col, pipe.frame[:n].clone()
+
+
+@pytest.mark.parametrize("dtype", [M.F32_REFINED, M.F64])
+@pytest.mark.parametrize("loss", ["laplacian", "random"])
+def test_position_gradient_matches_oracle(dtype, loss):
+    c = C.cube_on_sheet(0.04, cube=0.32, sheet=1.0)
+    ctx, d, rp, col, frame = _setup(c, dtype)
+    pos = d["pos_h"].clone().requires_grad_(True)
+    fields = d["fields"].clone().requires_grad_(True)
+    out = gfdm_operators(ctx, pos, fields, rp, col, d["model"], frame, dtype)
+    rng = np.random.default_rng(4)
+    Gr = rng.normal(size=(c.n, 4, 4))
+    if loss == "laplacian":
+        L = (out[:, :, 3] ** 2).sum()
+    else:
+        L = (out * torch.tensor(Gr, dtype=out.dtype, device="cuda")).sum()
+    L.backward()
+    gpos = pos.grad.double().cpu().numpy()
+    gfld = fields.grad.double().cpu().numpy()
+    # oracle on its own neighbours / stencils
+    P = c.pos_h.astype(np.float64)
+    orp, ocol = O.neighbours(P)
+    coef, status, _ = O.stencils(P, c.model, orp, ocol)
+    oout = O.apply(orp, ocol, coef, c.vp)
+    if loss == "laplacian":
+        G = np.zeros_like(oout)
+        G[:, :, 3] = 2.0 * oout[:, :, 3]
+    else:
+        G = Gr
+    og = O.stencil_grad(P, c.model, orp, ocol, c.vp, G)
+    ogf = O.apply_T(orp, ocol, coef, G)
+    tol = 2e-3 if dtype != M.F64 else 1e-8
+    scale = np.abs(og[:, :3]).max(0)
+    assert np.all(np.abs(gpos[:, :3] - og[:, :3]).max(0) <= tol * scale), \
+        (np.abs(gpos[:, :3] - og[:, :3]).max(0) / scale)
+    assert np.all(gpos[:, 3] == 0)
+    fscale = np.abs(ogf).max(0)
+    assert np.all(np.abs(gfld - ogf).max(0) <= tol * fscale), np.abs(gfld - ogf).max(0) / fscale
+    ctx.close()
+
+
+def test_gradcheck_fp64_tiny_cloud():
+    # FP64 forward and hand-written backward agree with torch's finite differences
+    c = C.cube_on_sheet(0.1, cube=0.5, sheet=1.0)        # 125 + 75 particles
+    ctx, d, rp, col, frame = _setup(c, M.F64)
+    pos = d["pos_h"].clone().requires_grad_(True)
+    fields = d["fields"].clone().requires_grad_(True)
+
+    def f(p, u):
+        # only x, y, z carry gradients; h enters as a constant
+        full = torch.cat([p, d["pos_h"][:, 3:]], 1)
+        return gfdm_operators(ctx, full.contiguous(), u, rp, col, d["model"], frame, M.F64)
+
+    xyz = pos[:, :3].detach().clone().requires_grad_(True)
+    assert torch.autograd.gradcheck(f, (xyz, fields), eps=1e-7, atol=1e-6, rtol=1e-5,
+                                    nondet_tol=1e-9, fast_mode=True)
+    ctx.close()
