@@ -41,6 +41,7 @@ APPLY_BYTES_NNZ = {4: 20, 8: 36}
 APPLY_BYTES_N = {4: 88, 8: 168}
 ST3_FLOP_NBR, ST3_FLOP_PART = 210.0, 1200.0
 ST2_FLOP_NBR, ST2_FLOP_PART = 90.0, 1000.0
+STG3_FLOP_NBR, STG3_FLOP_PART = 2.5 * ST3_FLOP_NBR, 2.5 * ST3_FLOP_PART  # adjoint ~2.5x forward
 NBR_FLOP_TEST = 11.0   # 3 sub, 2 fma + 1 mul (d^2), add + 2 mul (r^2), compare
 
 
@@ -355,19 +356,29 @@ def bench_gpu(args):
                                "unit": "TFLOP/s", "ms": ms, "algorithmic": fl,
                                "candidate_tests": n_cand,
                                "peak_src": "FP32 FMA issue rate at sampled clock"}
-    top = max(prof.items(), key=lambda kv: kv[1][1])
-    dominant = None
-    for key, pref in (("apply_ops", "k_apply<G="), ("build_stencils_3d", "k_stencil<f32,M=10"),
-                      ("build_stencils_2d", "k_stencil<f32,M=6"), ("nbr_mask", "k_nbr_mask<float>")):
-        if top[0].startswith(pref):
-            dominant = key
-    if dominant is None:
-        dominant = max(kernels, key=lambda k: kernels[k]["ms"]) if kernels else None
-    traffic = None
+    ms, _ = kernel_ms("k_stencil_grad<f32,M=10")
+    if ms:
+        fl = STG3_FLOP_NBR * nbr3 + STG3_FLOP_PART * n3
+        kernels["stencil_adjoint_3d"] = {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12,
+                                         "peak": fp32_peak, "unit": "TFLOP/s", "ms": ms,
+                                         "algorithmic": fl,
+                                         "peak_src": "FP32 FMA issue rate at sampled clock"}
+    # the dominant kernel: the largest share of the step among those with a roofline
+    dominant = max(kernels, key=lambda k: kernels[k]["ms"]) if kernels else None
+    traffic = {}
     try:
+        # DRAM bytes per launch from an ncu capture, valid only while the
+        # kernel's sources are unchanged since the capture
+        import hashlib
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f)
-    except OSError:
+            for k, v in json.load(f).items():
+                h = hashlib.sha256()
+                for src in (v["source"], "paper_2405_13165_gb300/csrc/stencil_common.cuh",
+                            "paper_2405_13165_gb300/csrc/internal.cuh"):
+                    h.update(open(os.path.join(ROOT, src), "rb").read())
+                if h.hexdigest()[:16] == v["source_sha"]:
+                    traffic[k] = v["bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
         traffic = {}
     roof = None
     if dominant:

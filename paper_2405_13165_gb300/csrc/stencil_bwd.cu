@@ -253,24 +253,38 @@ __global__ void __launch_bounds__(kStThreads) k_stencil_grad_redo(
 
 __global__ void k_reset_grad_queue(DevStatus *st) { st->fallback_count = 0; }
 
+template <typename TS, typename C, int M, int G, bool QUEUE>
+static void launch_grad_g(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void *pos_h,
+                          const uint8_t *model, const void *frame, const long long *rp,
+                          const int32_t *col, const void *fields, const void *gout, void *gpos,
+                          const StParams<C> &sp) {
+  using V = vec4_t<TS>;
+  static char name[64];
+  snprintf(name, sizeof(name), "k_stencil_grad<%s,M=%d,G=%d>", sizeof(TS) == 4 ? "f32" : "f64",
+           M, G);
+  MAFP_TIMED(ctx, s, name,
+             (k_stencil_grad<TS, C, M, G, QUEUE><<<grid_for(n * G, kStThreads, sm_count() * 64),
+                                                   kStThreads, 0, s>>>(
+                 n, (const V *)pos_h, model, (const V *)frame, rp, col, (const V *)fields,
+                 (const V *)gout, (TS *)gpos, sp, ctx->d_status, ctx->fallback)));
+}
+
+// Group sizes follow the context's tuning of the forward stencil build.
 template <typename TS, typename C, bool QUEUE>
 static void launch_grad(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void *pos_h,
                         const uint8_t *model, const void *frame, const long long *rp,
                         const int32_t *col, const void *fields, const void *gout, void *gpos,
                         const StParams<C> &sp) {
-  using V = vec4_t<TS>;
-  const int sms = sm_count();
-  constexpr int G3 = 16, G2 = 8;
-  MAFP_TIMED(ctx, s, sizeof(TS) == 4 ? "k_stencil_grad<f32,M=10>" : "k_stencil_grad<f64,M=10>",
-             (k_stencil_grad<TS, C, 10, G3, QUEUE><<<grid_for(n * G3, kStThreads, sms * 64),
-                                                    kStThreads, 0, s>>>(
-                 n, (const V *)pos_h, model, (const V *)frame, rp, col, (const V *)fields,
-                 (const V *)gout, (TS *)gpos, sp, ctx->d_status, ctx->fallback)));
-  MAFP_TIMED(ctx, s, sizeof(TS) == 4 ? "k_stencil_grad<f32,M=6>" : "k_stencil_grad<f64,M=6>",
-             (k_stencil_grad<TS, C, 6, G2, QUEUE><<<grid_for(n * G2, kStThreads, sms * 64),
-                                                   kStThreads, 0, s>>>(
-                 n, (const V *)pos_h, model, (const V *)frame, rp, col, (const V *)fields,
-                 (const V *)gout, (TS *)gpos, sp, ctx->d_status, ctx->fallback)));
+  switch (ctx->tune.stencil3d_group) {
+    case 8: launch_grad_g<TS, C, 10, 8, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
+    case 16: launch_grad_g<TS, C, 10, 16, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
+    default: launch_grad_g<TS, C, 10, 32, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
+  }
+  switch (ctx->tune.stencil2d_group) {
+    case 4: launch_grad_g<TS, C, 6, 4, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
+    case 16: launch_grad_g<TS, C, 6, 16, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
+    default: launch_grad_g<TS, C, 6, 8, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
+  }
 }
 
 int build_stencils_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h,
