@@ -139,6 +139,30 @@ int mafp_build_neighbours(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *p
                           int64_t *row_ptr, int32_t *col, int64_t cap_nnz, int64_t *nnz_dev,
                           int32_t *order, void *stream);
 
+/* Largest nclouds of mafp_build_neighbours_batched. */
+#define MAFP_MAX_CLOUDS 65536
+
+/* --------------------------------------------------------------------------
+ * mafp_build_neighbours_batched -- Eq. Nbd for nclouds independent clouds
+ * stored back to back: cloud b owns particles [cloud_offset[b],
+ * cloud_offset[b+1]), and S_i only ever holds particles of i's own cloud
+ * (each cloud gets its own bounding box and cell grid, and the clouds' cells
+ * are numbered one after another), so overlapping clouds do not interact.
+ * Batching has no counterpart in the paper: one launch per stage serves many
+ * small clouds that would each leave most of the GPU idle.
+ *   cloud_offset int64 [nclouds+1] DEVICE: cloud_offset[0] = 0,
+ *            cloud_offset[nclouds] = n, non-decreasing (empty clouds allowed);
+ *            otherwise the status block records MAFP_EINVAL, col and order
+ *            are not written and row_ptr is unspecified
+ *   the other arguments as mafp_build_neighbours, indices global over all
+ *   clouds.  cap_cells of the context bounds the sum of all clouds' cells.
+ * nclouds outside [1, MAFP_MAX_CLOUDS] -> MAFP_EINVAL on the host.
+ * mafp_build_neighbours is this call with nclouds = 1. */
+int mafp_build_neighbours_batched(mafp_ctx *ctx, int64_t n, int32_t dtype, int32_t nclouds,
+                                  const int64_t *cloud_offset, const void *pos_h,
+                                  int64_t *row_ptr, int32_t *col, int64_t cap_nnz,
+                                  int64_t *nnz_dev, int32_t *order, void *stream);
+
 /* --------------------------------------------------------------------------
  * mafp_classify_pca -- model-transition detection of Sec. 4:
  *  3D wall particles: Alg. 2 -- resolution criterion (Sec. 4.1.1) over 3D

@@ -369,6 +369,38 @@ def config_diff_2m(seed: int = SEED_BASE + 4) -> Cloud:
     return cube_on_sheet(mid, seed=seed)
 
 
+def batched_clouds(nclouds: int = 256, n_lo: int = 2_000, n_hi: int = 200_000,
+                   film_lo: float = 0.1, film_hi: float = 0.9, dx: float = 0.02,
+                   seed: int = SEED_BASE + 3) -> list[Cloud]:
+    """Independent cube-on-sheet clouds of uneven size and model mix.
+
+    Cloud b draws N_b log-uniform in [n_lo, n_hi] and a film fraction f_b
+    uniform in [film_lo, film_hi] (from `seed`), then sizes the shape at the
+    spacing dx: cube edge m = round(((1 - f_b) N_b)^(1/3)) cells, sheet edge
+    s = round(sqrt(f_b N_b + m^2)) cells.  Its lattice, jitter and fields use
+    seed 1000 * 3 + b above the base seed.  Every cloud sits at the same place,
+    so clouds overlap in space and only the batching keeps them apart.
+    """
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=nclouds))
+    films = rng.uniform(film_lo, film_hi, size=nclouds)
+    out = []
+    for b in range(nclouds):
+        m = max(2, int(round(((1.0 - films[b]) * sizes[b]) ** (1.0 / 3.0))))
+        s = max(m + 2, int(round(math.sqrt(films[b] * sizes[b] + m * m))))
+        out.append(cube_on_sheet(dx, cube=m * dx, sheet=s * dx, seed=SEED_BASE + 3 * 1000 + b))
+    return out
+
+
+def config_batched(nclouds: int = 256, **kw) -> tuple[Cloud, np.ndarray]:
+    """The batched workload: `batched_clouds` each put in its own cell order and
+    stored back to back; returns (cloud, int64 offsets [nclouds + 1])."""
+    parts = [cell_sorted(c) for c in batched_clouds(nclouds, **kw)]
+    off = np.zeros(len(parts) + 1, np.int64)
+    off[1:] = np.cumsum([c.n for c in parts])
+    return concat(parts, f"batched({len(parts)} clouds)"), off
+
+
 def cell_sorted(cloud: Cloud, cell_factor: float = 1.0 + 1e-6) -> Cloud:
     """Permute a cloud into cell order: cells of edge max(h) * cell_factor from
     the bounding-box minimum, keys (cz * ny + cy) * nx + cx, stable in index.

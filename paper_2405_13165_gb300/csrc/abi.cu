@@ -11,6 +11,8 @@
 namespace mafp {
 int build_neighbours(mafp_ctx *, int64_t, int32_t, const void *, int64_t *, int32_t *, int64_t,
                      int64_t *, int32_t *, cudaStream_t);
+int build_neighbours_batched(mafp_ctx *, int64_t, int32_t, int32_t, const int64_t *, const void *,
+                             int64_t *, int32_t *, int64_t, int64_t *, int32_t *, cudaStream_t);
 int transpose_map(mafp_ctx *, int64_t, const int64_t *, const int32_t *, uint16_t *,
                   cudaStream_t);
 int classify_pca(mafp_ctx *, int64_t, int32_t, const void *, const uint8_t *, const uint8_t *,
@@ -46,6 +48,7 @@ int sm_count() {
 }  // namespace mafp
 
 using namespace mafp;
+static_assert(kMaxClouds == MAFP_MAX_CLOUDS, "batch limit of the header and the library differ");
 
 static const char *kNoCtx = "null context";
 
@@ -137,10 +140,14 @@ int mafp_create(mafp_ctx **out, const mafp_params *params, int64_t cap_particles
       {(void **)&ctx->nbr_mask, sizeof(uint32_t) * kMaskWords * cap},
       {(void **)&ctx->overflow, sizeof(int32_t) * cap},
       {(void **)&ctx->scan_tmp, sizeof(long long) * (i64_len / 4096 + 4)},
-      {(void **)&ctx->bbox_partial, sizeof(double) * 1024 * 8},
       {(void **)&ctx->fallback, sizeof(int32_t) * cap},
       {(void **)&ctx->d_status, sizeof(DevStatus)},
       {(void **)&ctx->d_grid, sizeof(GridDev)},
+      {(void **)&ctx->d_grids, sizeof(GridDev) * kMaxClouds},
+      {(void **)&ctx->cell_base, sizeof(long long) * (kMaxClouds + 1)},
+      {(void **)&ctx->cloud_id, sizeof(int32_t) * cap},
+      {(void **)&ctx->one_cloud, sizeof(long long) * 2},
+      {(void **)&ctx->cloud_partial, sizeof(double) * (kMaxClouds + 1024) * 8},
       {(void **)&ctx->remap_i64, sizeof(int64_t) * i64_len},
       {(void **)&ctx->remap_i32, sizeof(int32_t) * 3 * cap},
   };
@@ -168,8 +175,9 @@ int mafp_destroy(mafp_ctx *ctx) {
                   ctx->radix_hist, ctx->cell_start, ctx->cell_end,   ctx->spos,
                   ctx->ucell,     ctx->n_ucell,  ctx->counts,       ctx->scan_tmp,
                   ctx->nbr_mask,  ctx->overflow,
-                  ctx->bbox_partial, ctx->fallback, ctx->d_status,  ctx->d_grid,
-                  ctx->remap_i64, ctx->remap_i32};
+                  ctx->fallback, ctx->d_status,  ctx->d_grid,
+                  ctx->remap_i64, ctx->remap_i32, ctx->d_grids,   ctx->cell_base,
+                  ctx->cloud_id,  ctx->one_cloud, ctx->cloud_partial};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ctx->prof_ev) {
@@ -246,6 +254,30 @@ int mafp_build_neighbours(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *p
   REQUIRE(pos_h);
   REQUIRE(col);
   return build_neighbours(ctx, n, dtype, pos_h, row_ptr, col, cap_nnz, nnz_dev, order, s);
+}
+
+int mafp_build_neighbours_batched(mafp_ctx *ctx, int64_t n, int32_t dtype, int32_t nclouds,
+                                  const int64_t *cloud_offset, const void *pos_h,
+                                  int64_t *row_ptr, int32_t *col, int64_t cap_nnz,
+                                  int64_t *nnz_dev, int32_t *order, void *stream) {
+  if (!ctx) return MAFP_EINVAL;
+  int rc;
+  if ((rc = check_dtype(ctx, dtype)) || (rc = check_n(ctx, n))) return rc;
+  if (nclouds < 1 || nclouds > kMaxClouds) return fail(ctx, MAFP_EINVAL, "nclouds out of range");
+  REQUIRE(row_ptr);
+  REQUIRE(cloud_offset);
+  if (cap_nnz < 0) return fail(ctx, MAFP_EINVAL, "negative cap_nnz");
+  if (ensure_device(ctx)) return MAFP_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    MAFP_CUDA_TRY(ctx, cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), s));
+    if (nnz_dev) MAFP_CUDA_TRY(ctx, cudaMemsetAsync(nnz_dev, 0, sizeof(int64_t), s));
+    return MAFP_OK;
+  }
+  REQUIRE(pos_h);
+  REQUIRE(col);
+  return build_neighbours_batched(ctx, n, dtype, nclouds, cloud_offset, pos_h, row_ptr, col,
+                                  cap_nnz, nnz_dev, order, s);
 }
 
 int mafp_classify_pca(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h,

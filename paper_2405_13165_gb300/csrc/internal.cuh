@@ -11,6 +11,7 @@ namespace mafp {
 constexpr int kMaxRowSort = 2048;   // longest row the in-shared-memory row sort handles
 constexpr int kMaskCap = 1536;      // candidates of one cell tile in the neighbour mask kernel
 constexpr int kMaskWords = kMaskCap / 32;
+constexpr int kMaxClouds = 65536;   // clouds of one batched neighbour build
 
 // Device status block (layout mirrored by mafp_status in the public header).
 struct DevStatus {
@@ -65,10 +66,14 @@ struct mafp_ctx {
   uint32_t *nbr_mask;       // [kMaskWords * cap] candidate hit bits, word-major
   int32_t *overflow;        // [cap] occupied cells whose candidates overflow the tile
   long long *scan_tmp;      // [cap/1024 + 2]
-  double *bbox_partial;     // [1024 * 8]
   int32_t *fallback;        // [cap] particles re-done in FP64
   mafp::DevStatus *d_status;
-  mafp::GridDev *d_grid;
+  mafp::GridDev *d_grid;     // all-clouds flag and totals
+  mafp::GridDev *d_grids;    // [kMaxClouds] one grid per cloud
+  long long *cell_base;      // [kMaxClouds + 1] first global cell of each cloud
+  int32_t *cloud_id;         // [cap] cloud of every particle
+  long long *one_cloud;      // [2] offsets of the single-cloud case
+  double *cloud_partial;     // [(kMaxClouds + 1024) * 8] bounding-box partials
   int64_t *remap_i64;       // [3 * cap + 8]
   int32_t *remap_i32;       // [2 * cap]
   char err[512];

@@ -3,6 +3,7 @@
 // -> count (one block per occupied cell, candidate tiles staged in shared
 // memory) -> exclusive scan -> fill -> (row sort when the input order is not
 // the cell order) ; plus the transpose map used by the apply adjoint.
+#include <algorithm>
 #include <climits>
 
 #include "internal.cuh"
@@ -13,12 +14,37 @@ namespace mafp {
 constexpr int kBoxThreads = 256;
 constexpr int kBoxBlocks = 1024;
 
+// ------------------------------------------------ several clouds, one grid each
+// Cloud b owns particles [off[b], off[b+1]) and cells [cell_base[b], cell_base[b+1])
+// of the global cell numbering, with its own bounding box and cell edge, so
+// neighbourhoods never cross clouds.  A single cloud is the case nb = 1.
+struct CloudGrids {
+  const GridDev *grids;      // [nb]
+  const long long *cell_base;  // [nb + 1]
+  int nb;
+  const GridDev *all;        // ok flag and total cell count
+};
+
+__global__ void k_set_one_cloud(long long *off, int64_t n) {
+  off[0] = 0;
+  off[1] = n;
+}
+
+// Block (b, part) reduces part `part` of cloud b: min / max of x, y, z, max h,
+// count of non-finite entries; also records each particle's cloud.
 template <typename T>
-__global__ void __launch_bounds__(kBoxThreads) k_bbox(const vec4_t<T> *pos, int64_t n,
-                                                      double *partial) {
+__global__ void __launch_bounds__(kBoxThreads) k_cloud_bbox(const vec4_t<T> *pos, int64_t n,
+                                                            const long long *off, int nb,
+                                                            int parts, double *partial,
+                                                            int32_t *cloud_id) {
+  const int b = blockIdx.x / parts, part = blockIdx.x % parts;
+  // offsets are checked in k_cloud_grid; clamping keeps every access in [0, n)
+  const long long lo = max(0LL, min(off[b], (long long)n));
+  const long long hi = max(lo, min(off[b + 1], (long long)n));
   double v[8] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0, 0.0};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (long long i = lo + (long long)part * blockDim.x + threadIdx.x; i < hi;
+       i += (long long)parts * blockDim.x) {
+    cloud_id[i] = b;
     vec4_t<T> p = ld4(pos + i);
     bool ok = isfinite((double)p.x) && isfinite((double)p.y) && isfinite((double)p.z) &&
               isfinite((double)p.w) && p.w > T(0);
@@ -39,102 +65,169 @@ __global__ void __launch_bounds__(kBoxThreads) k_bbox(const vec4_t<T> *pos, int6
     v[7] += __shfl_xor_sync(0xffffffffu, v[7], o);
   }
   __shared__ double red[kBoxThreads / 32][8];
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0)
-    for (int k = 0; k < 8; ++k) red[w][k] = v[k];
-  __syncthreads();
-  if (threadIdx.x < 8) {
-    int k = threadIdx.x;
-    double a = red[0][k];
-    for (int ww = 1; ww < kBoxThreads / 32; ++ww)
-      a = k < 3 ? fmin(a, red[ww][k]) : (k < 7 ? fmax(a, red[ww][k]) : a + red[ww][k]);
-    partial[blockIdx.x * 8 + k] = a;
-  }
-}
-
-// One block of kBoxThreads threads reduces the per-block partials and sets the grid.
-__global__ void __launch_bounds__(kBoxThreads) k_grid(const double *partial, int nb, GridDev *g,
-                                                      DevStatus *st, long long cap_cells) {
-  double v[8] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0, 0.0};
-  for (int b = threadIdx.x; b < nb; b += blockDim.x)
-    for (int k = 0; k < 8; ++k) {
-      double a = partial[b * 8 + k];
-      v[k] = k < 3 ? fmin(v[k], a) : (k < 7 ? fmax(v[k], a) : v[k] + a);
-    }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) v[k] = fmin(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
-#pragma unroll
-    for (int k = 3; k < 7; ++k) v[k] = fmax(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
-    v[7] += __shfl_xor_sync(0xffffffffu, v[7], o);
-  }
-  __shared__ double red[kBoxThreads / 32][8];
   if ((threadIdx.x & 31) == 0)
     for (int k = 0; k < 8; ++k) red[threadIdx.x >> 5][k] = v[k];
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  for (int w = 1; w < kBoxThreads / 32; ++w)
-    for (int k = 0; k < 8; ++k)
-      v[k] = k < 3 ? fmin(v[k], red[w][k]) : (k < 7 ? fmax(v[k], red[w][k]) : v[k] + red[w][k]);
-  g->ok = 0;
-  if (v[7] > 0.0) {
-    st->n_nonfinite += (long long)v[7];
-    set_error(st, MAFP_ENONFINITE, (long long)v[7]);
-    return;
+  if (threadIdx.x < 8) {
+    const int k = threadIdx.x;
+    double a = red[0][k];
+    for (int w = 1; w < kBoxThreads / 32; ++w)
+      a = k < 3 ? fmin(a, red[w][k]) : (k < 7 ? fmax(a, red[w][k]) : a + red[w][k]);
+    partial[(long long)blockIdx.x * 8 + k] = a;
   }
-  // Strictly larger than every support radius (h_i + h_j)/2 <= max h, so every
-  // member of S_i lies in the 27 cells around i's cell.
-  double c = v[6] * (1.0 + 1e-6);
-  long long ncells = 0;
-  int dim[3];
-  for (int it = 0; it < 64; ++it) {
-    double cells = 1.0;
-    for (int a = 0; a < 3; ++a) {
-      double d = floor((v[3 + a] - v[a]) / c) + 1.0;
-      cells *= d;
-      dim[a] = d < 2e9 ? (int)d : INT_MAX;
-    }
-    if (cells <= (double)cap_cells) {
-      ncells = (long long)dim[0] * dim[1] * dim[2];
-      break;
-    }
-    c *= cbrt(cells / (double)cap_cells) * 1.0001;
+}
+
+// Cells of cloud b at edge c (>= max h of the cloud); 0 for an empty cloud.
+__device__ double cloud_cells(const double v[8], double c, int dim[3]) {
+  if (!(v[6] > 0.0)) {
+    dim[0] = dim[1] = dim[2] = 1;
+    return 0.0;
   }
-  if (ncells <= 0) {
-    set_error(st, MAFP_ECAPACITY, cap_cells);
-    return;
-  }
+  double cells = 1.0;
   for (int a = 0; a < 3; ++a) {
-    g->lo[a] = v[a];
-    g->dim[a] = dim[a];
+    const double d = floor((v[3 + a] - v[a]) / c) + 1.0;
+    cells *= d;
+    dim[a] = d < 2e9 ? (int)d : INT_MAX;
   }
-  g->c = c;
-  g->inv_c = 1.0 / c;
-  g->ncells = ncells;
-  g->hmax = v[6];
-  g->ok = 1;
-  st->ncells = ncells;
-  st->cell_size = c;
-  st->not_identity = 0;
+  return cells;
+}
+
+// One block: per-cloud bounding boxes and grids, the global cell numbering
+// (exclusive scan of the clouds' cell counts) and the all-clouds flag.  The cell
+// edge of every cloud starts strictly above its max h (so S_i lies in the 27
+// cells around i's cell) and grows uniformly when the total exceeds cap_cells.
+__global__ void __launch_bounds__(kBoxThreads) k_cloud_grid(const double *partial,
+                                                            const long long *off, int64_t n,
+                                                            int nb, int parts, GridDev *grids,
+                                                            long long *cell_base, GridDev *all,
+                                                            DevStatus *st, long long cap_cells) {
+  __shared__ double s_nonfinite, s_cells;
+  __shared__ double s_scale;
+  __shared__ int s_bad;
+  __shared__ long long s_sum[kBoxThreads];
+  if (threadIdx.x == 0) {
+    s_nonfinite = 0.0;
+    s_scale = 1.0;
+    s_bad = (off[0] != 0 || off[nb] != n) ? 1 : 0;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+    if (off[b + 1] < off[b]) s_bad = 1;
+  __syncthreads();
+  if (s_bad) {
+    // the offsets do not split [0, n) into consecutive ranges
+    if (threadIdx.x == 0) {
+      all->ok = 0;
+      set_error(st, MAFP_EINVAL, -1);
+    }
+    return;
+  }
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    double v[8] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0, 0.0};
+    for (int q = 0; q < parts; ++q)
+      for (int k = 0; k < 8; ++k) {
+        const double a = partial[((long long)b * parts + q) * 8 + k];
+        v[k] = k < 3 ? fmin(v[k], a) : (k < 7 ? fmax(v[k], a) : v[k] + a);
+      }
+    if (v[7] > 0.0) atomicAdd(&s_nonfinite, v[7]);
+    GridDev &g = grids[b];
+    for (int a = 0; a < 3; ++a) g.lo[a] = v[a] < INFINITY ? v[a] : 0.0;
+    g.hmax = v[6];
+    g.c = v[6] * (1.0 + 1e-6);
+    g.inv_c = v[6] > 0.0 ? 1.0 / g.c : 1.0;
+    // stash the box in the grid record until the edge is final
+    g.dim[0] = g.dim[1] = g.dim[2] = 1;
+  }
+  __syncthreads();
+  if (s_nonfinite > 0.0) {
+    if (threadIdx.x == 0) {
+      all->ok = 0;
+      st->n_nonfinite += (long long)s_nonfinite;
+      set_error(st, MAFP_ENONFINITE, (long long)s_nonfinite);
+    }
+    return;
+  }
+  for (int it = 0; it < 64; ++it) {
+    if (threadIdx.x == 0) s_cells = 0.0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      double v[8] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0, 0.0};
+      for (int q = 0; q < parts; ++q)
+        for (int k = 0; k < 7; ++k) {
+          const double a = partial[((long long)b * parts + q) * 8 + k];
+          v[k] = k < 3 ? fmin(v[k], a) : fmax(v[k], a);
+        }
+      int dim[3];
+      const double c = v[6] * (1.0 + 1e-6) * s_scale;
+      const double cells = cloud_cells(v, c, dim);
+      GridDev &g = grids[b];
+      g.c = c;
+      g.inv_c = v[6] > 0.0 ? 1.0 / c : 1.0;
+      for (int a = 0; a < 3; ++a) g.dim[a] = dim[a];
+      g.ncells = (long long)cells;
+      g.ok = 1;
+      atomicAdd(&s_cells, cells);
+    }
+    __syncthreads();
+    const bool fits = s_cells <= (double)cap_cells;
+    __syncthreads();
+    if (fits) break;
+    if (threadIdx.x == 0) s_scale *= cbrt(s_cells / (double)cap_cells) * 1.0001;
+    __syncthreads();
+  }
+  // exclusive scan of the cell counts: thread t takes a contiguous chunk
+  const int chunk = (nb + kBoxThreads - 1) / kBoxThreads;
+  const int b0 = threadIdx.x * chunk, b1 = min(nb, b0 + chunk);
+  long long part_sum = 0;
+  for (int b = b0; b < b1; ++b) part_sum += grids[b].ncells;
+  s_sum[threadIdx.x] = part_sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    for (int t = 0; t < kBoxThreads; ++t) {
+      const long long v = s_sum[t];
+      s_sum[t] = acc;
+      acc += v;
+    }
+  }
+  __syncthreads();
+  long long run = s_sum[threadIdx.x];
+  for (int b = b0; b < b1; ++b) {
+    cell_base[b] = run;
+    run += grids[b].ncells;
+  }
+  if (threadIdx.x == 0) {
+    long long acc = s_sum[kBoxThreads - 1];
+    for (int b = (kBoxThreads - 1) * chunk; b < nb; ++b) acc += grids[b].ncells;
+    cell_base[nb] = acc;
+    all->ok = acc <= cap_cells ? 1 : 0;
+    all->ncells = acc;
+    all->c = grids[0].c;
+    if (acc > cap_cells) set_error(st, MAFP_ECAPACITY, cap_cells);
+    st->ncells = acc;
+    st->cell_size = grids[0].c;
+    st->not_identity = 0;
+  }
 }
 
 template <typename T>
-__global__ void k_hash(const vec4_t<T> *pos, int64_t n, const GridDev *g, uint32_t *keys,
-                       int32_t *vals) {
-  if (!g->ok) return;
+__global__ void k_hash(const vec4_t<T> *pos, int64_t n, const int32_t *cloud_id, CloudGrids cg,
+                       uint32_t *keys, int32_t *vals) {
+  if (!cg.all->ok) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = cloud_id[i];
+    const GridDev &g = cg.grids[b];
     vec4_t<T> p = ld4(pos + i);
     double q[3] = {(double)p.x, (double)p.y, (double)p.z};
     long long c[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      long long v = (long long)floor((q[a] - g->lo[a]) * g->inv_c);
-      v = v < 0 ? 0 : (v >= g->dim[a] ? g->dim[a] - 1 : v);
+      long long v = (long long)floor((q[a] - g.lo[a]) * g.inv_c);
+      v = v < 0 ? 0 : (v >= g.dim[a] ? g.dim[a] - 1 : v);
       c[a] = v;
     }
-    keys[i] = (uint32_t)((c[2] * g->dim[1] + c[1]) * g->dim[0] + c[0]);
+    keys[i] = (uint32_t)(cg.cell_base[b] + (c[2] * g.dim[1] + c[1]) * g.dim[0] + c[0]);
     vals[i] = (int32_t)i;
   }
 }
@@ -274,9 +367,14 @@ constexpr int kNbrSmemBytes = 32768;
 // Warp-per-particle count / fill (ballot compaction), for the occupied cells
 // listed in sel[0 .. *n_sel): the cells whose 27-cell candidate union does not
 // fit the shared-memory tile of the mask kernel below.
+struct CloudGrids;
+__device__ __forceinline__ void cell_runs(int key, const CloudGrids &cg,
+                                          const int32_t *cell_start, const int32_t *cell_end,
+                                          int r, int *lo_out, int *len_out);
+
 template <typename T, bool FILL>
 __global__ void __launch_bounds__(kNbrThreads) k_nbr(
-    const GridDev *g, const int32_t *ucell, const int32_t *sel, const int32_t *n_sel,
+    CloudGrids cg, const int32_t *ucell, const int32_t *sel, const int32_t *n_sel,
     const vec4_t<T> *spos, const int32_t *svals, const int32_t *cell_start,
     const int32_t *cell_end, int32_t *counts, const long long *row_ptr, int32_t *col,
     long long cap_nnz, int64_t n) {
@@ -285,31 +383,17 @@ __global__ void __launch_bounds__(kNbrThreads) k_nbr(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *cand = reinterpret_cast<V *>(smem_raw);
   __shared__ int r_lo[9], r_len[9], r_off[10];
-  if (!g->ok) return;
+  if (!cg.all->ok) return;
   if (FILL && row_ptr[n] > cap_nnz) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = kNbrThreads / 32;
   const unsigned lt = (1u << lane) - 1u;
   const int nu = *n_sel;
-  const int dx_ = g->dim[0], dy_ = g->dim[1], dz_ = g->dim[2];
   for (int cs = blockIdx.x; cs < nu; cs += gridDim.x) {
     const int cb = sel[cs];
     const int key = ucell[2 * cb], s0 = ucell[2 * cb + 1];
     const int s1 = cell_end[key];
-    const int cx = key % dx_, cy = (key / dx_) % dy_, cz = key / (dx_ * dy_);
-    if (threadIdx.x < 9) {
-      const int r = threadIdx.x, ddz = r / 3 - 1, ddy = r % 3 - 1;
-      int lo = INT_MAX, hi = 0;
-      if (cz + ddz >= 0 && cz + ddz < dz_ && cy + ddy >= 0 && cy + ddy < dy_) {
-        const int base = key + ddz * dx_ * dy_ + ddy * dx_;
-        const int k0 = cx > 0 ? base - 1 : base, k1 = cx < dx_ - 1 ? base + 1 : base;
-        for (int k = k0; k <= k1; ++k) {
-          lo = min(lo, cell_start[k]);
-          hi = max(hi, cell_end[k]);
-        }
-      }
-      r_lo[r] = lo;
-      r_len[r] = hi > lo ? hi - lo : 0;
-    }
+    if (threadIdx.x < 9)
+      cell_runs(key, cg, cell_start, cell_end, threadIdx.x, &r_lo[threadIdx.x], &r_len[threadIdx.x]);
     __syncthreads();
     if (threadIdx.x == 0) {
       int o = 0;
@@ -374,13 +458,21 @@ constexpr int kMaskThreads = 64;
 constexpr int kExpThreads = 128;
 constexpr int kExpChunk = 64;             // particles of a cell expanded per round
 
-// Rows of the 27-cell neighbourhood of cell `key`: run r (dz = r/3-1,
-// dy = r%3-1) covers cells key-1..key+1 of that (y, z) row, clipped to the grid.
-__device__ __forceinline__ void cell_runs(int key, const GridDev *g, const int32_t *cell_start,
-                                          const int32_t *cell_end, int r, int *lo_out,
-                                          int *len_out) {
-  const int dx_ = g->dim[0], dy_ = g->dim[1], dz_ = g->dim[2];
-  const int cx = key % dx_, cy = (key / dx_) % dy_, cz = key / (dx_ * dy_);
+// Rows of the 27-cell neighbourhood of global cell `key`: run r (dz = r/3-1,
+// dy = r%3-1) covers cells key-1..key+1 of that (y, z) row of the key's own
+// cloud grid, clipped to that grid.
+__device__ __forceinline__ void cell_runs(int key, const CloudGrids &cg,
+                                          const int32_t *cell_start, const int32_t *cell_end,
+                                          int r, int *lo_out, int *len_out) {
+  int b0 = 0, b1 = cg.nb;   // cloud with cell_base[b] <= key < cell_base[b + 1]
+  while (b1 - b0 > 1) {
+    const int mid = (b0 + b1) >> 1;
+    if (cg.cell_base[mid] <= key) b0 = mid; else b1 = mid;
+  }
+  const GridDev &g = cg.grids[b0];
+  const int local = key - (int)cg.cell_base[b0];
+  const int dx_ = g.dim[0], dy_ = g.dim[1], dz_ = g.dim[2];
+  const int cx = local % dx_, cy = (local / dx_) % dy_, cz = local / (dx_ * dy_);
   const int ddz = r / 3 - 1, ddy = r % 3 - 1;
   int lo = INT_MAX, hi = 0;
   if (cz + ddz >= 0 && cz + ddz < dz_ && cy + ddy >= 0 && cy + ddy < dy_) {
@@ -412,20 +504,20 @@ __device__ __forceinline__ bool support_test(const double4_16a &a, const double4
 
 template <typename T>
 __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
-    const GridDev *g, const int32_t *ucell, const int32_t *n_ucell, const vec4_t<T> *spos,
+    CloudGrids cg, const int32_t *ucell, const int32_t *n_ucell, const vec4_t<T> *spos,
     const int32_t *svals, const int32_t *cell_start, const int32_t *cell_end, int32_t *counts,
     uint32_t *mask, int64_t stride, int32_t *overflow, int32_t *n_overflow) {
   using V = vec4_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *cand = reinterpret_cast<V *>(smem_raw);
   __shared__ int r_lo[9], r_len[9], r_off[10];
-  if (!g->ok) return;
+  if (!cg.all->ok) return;
   const int tid = threadIdx.x;
   const int nu = *n_ucell;
   for (int cb = blockIdx.x; cb < nu; cb += gridDim.x) {
     const int key = ucell[2 * cb], s0 = ucell[2 * cb + 1];
     const int s1 = cell_end[key];
-    if (tid < 9) cell_runs(key, g, cell_start, cell_end, tid, &r_lo[tid], &r_len[tid]);
+    if (tid < 9) cell_runs(key, cg, cell_start, cell_end, tid, &r_lo[tid], &r_len[tid]);
     __syncthreads();
     if (tid == 0) {
       int o = 0;
@@ -491,13 +583,13 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
 
 template <typename T>
 __global__ void __launch_bounds__(kExpThreads) k_nbr_expand(
-    const GridDev *g, const int32_t *ucell, const int32_t *n_ucell, const int32_t *svals,
+    CloudGrids cg, const int32_t *ucell, const int32_t *n_ucell, const int32_t *svals,
     const int32_t *cell_start, const int32_t *cell_end, const uint32_t *mask, int64_t stride,
     const long long *row_ptr, int32_t *col, long long cap_nnz, int64_t n) {
   __shared__ int r_lo[9], r_len[9], r_off[10];
   __shared__ uint32_t mw[kMaskWords][kExpChunk];
   __shared__ int32_t cand_v[kMaskCap];   // original index of every candidate of the cell
-  if (!g->ok) return;
+  if (!cg.all->ok) return;
   if (row_ptr[n] > cap_nnz) return;
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -505,7 +597,7 @@ __global__ void __launch_bounds__(kExpThreads) k_nbr_expand(
   for (int cb = blockIdx.x; cb < nu; cb += gridDim.x) {
     const int key = ucell[2 * cb], s0 = ucell[2 * cb + 1];
     const int s1 = cell_end[key];
-    if (tid < 9) cell_runs(key, g, cell_start, cell_end, tid, &r_lo[tid], &r_len[tid]);
+    if (tid < 9) cell_runs(key, cg, cell_start, cell_end, tid, &r_lo[tid], &r_len[tid]);
     __syncthreads();
     if (tid == 0) {
       int o = 0;
@@ -552,8 +644,8 @@ constexpr int kSortWarps = 4;
 __global__ void __launch_bounds__(kSortWarps * 32) k_rowsort(const long long *row_ptr,
                                                              int32_t *col, int64_t n,
                                                              long long cap_nnz,
-                                                             DevStatus *st) {
-  if (!st->not_identity) return;
+                                                             DevStatus *st, const GridDev *g) {
+  if (!g->ok || !st->not_identity) return;
   if (row_ptr[n] > cap_nnz) return;
   __shared__ int32_t buf[kSortWarps][kMaxRowSort];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -617,23 +709,29 @@ __global__ void k_tmap(const long long *row_ptr, const int32_t *col, int64_t n, 
 
 // ------------------------------------------------------------------ host side
 template <typename T>
-static int build_neighbours_t(mafp_ctx *ctx, int64_t n, const void *pos_h, int64_t *row_ptr,
-                              int32_t *col, int64_t cap_nnz, int64_t *nnz_dev, int32_t *order,
-                              cudaStream_t s) {
+static int build_neighbours_t(mafp_ctx *ctx, int64_t n, int nb, const long long *cloud_off,
+                              const void *pos_h, int64_t *row_ptr, int32_t *col,
+                              int64_t cap_nnz, int64_t *nnz_dev, int32_t *order, cudaStream_t s) {
   using V = vec4_t<T>;
   const V *pos = reinterpret_cast<const V *>(pos_h);
   const int sms = sm_count();
-  const int nb_box = grid_for(n, kBoxThreads, kBoxBlocks);
-  MAFP_TIMED(ctx, s, "k_bbox<T>",
-             k_bbox<T><<<nb_box, kBoxThreads, 0, s>>>(pos, n, ctx->bbox_partial));
-  MAFP_TIMED(ctx, s, "k_grid",
-             k_grid<<<1, kBoxThreads, 0, s>>>(ctx->bbox_partial, nb_box, ctx->d_grid, ctx->d_status, ctx->cap_cells));
-  MAFP_TIMED(ctx, s, "k_hash<T>",
-             k_hash<T><<<grid_for(n, 256, sms * 16), 256, 0, s>>>(pos, n, ctx->d_grid, ctx->keys_a,
-                                                       ctx->vals_a));
+  const int parts = std::max(1, std::min(kBoxBlocks / std::max(nb, 1), 64));
+  MAFP_TIMED(ctx, s, "k_cloud_bbox",
+             k_cloud_bbox<T><<<nb * parts, kBoxThreads, 0, s>>>(pos, n, cloud_off, nb, parts,
+                                                                 ctx->cloud_partial,
+                                                                 ctx->cloud_id));
+  MAFP_TIMED(ctx, s, "k_cloud_grid",
+             k_cloud_grid<<<1, kBoxThreads, 0, s>>>(ctx->cloud_partial, cloud_off, n, nb, parts,
+                                                    ctx->d_grids,
+                                                    ctx->cell_base, ctx->d_grid, ctx->d_status,
+                                                    ctx->cap_cells));
+  CloudGrids cg{ctx->d_grids, ctx->cell_base, nb, ctx->d_grid};
+  MAFP_TIMED(ctx, s, "k_hash",
+             k_hash<T><<<grid_for(n, 256, sms * 16), 256, 0, s>>>(pos, n, ctx->cloud_id, cg,
+                                                                  ctx->keys_a, ctx->vals_a));
   MAFP_TIMED(ctx, s, "k_clear_cells",
              k_clear_cells<<<sms * 8, 256, 0, s>>>(ctx->d_grid, ctx->cell_start, ctx->cell_end,
-                                        ctx->n_ucell));
+                                                   ctx->n_ucell));
   MAFP_LAUNCH_CHECK(ctx);
   const int tiles = (int)((n + kRadixTile - 1) / kRadixTile);
   uint32_t *kin = ctx->keys_a, *kout = ctx->keys_b;
@@ -665,11 +763,11 @@ static int build_neighbours_t(mafp_ctx *ctx, int64_t n, const void *pos_h, int64
   const int64_t stride = ctx->cap_particles;
   MAFP_TIMED(ctx, s, sizeof(T) == 4 ? "k_nbr_mask<float>" : "k_nbr_mask<double>",
              k_nbr_mask<T><<<sms * 16, kMaskThreads, kMaskCap * sizeof(V), s>>>(
-                 ctx->d_grid, ctx->ucell, ctx->n_ucell, spos, vin, ctx->cell_start,
+                 cg, ctx->ucell, ctx->n_ucell, spos, vin, ctx->cell_start,
                  ctx->cell_end, ctx->counts, ctx->nbr_mask, stride, ctx->overflow, n_overflow));
   MAFP_TIMED(ctx, s, "k_nbr<T,false>(overflow cells)",
              k_nbr<T, false><<<nbr_blocks, kNbrThreads, kNbrSmemBytes, s>>>(
-      ctx->d_grid, ctx->ucell, ctx->overflow, n_overflow, spos, vin, ctx->cell_start,
+      cg, ctx->ucell, ctx->overflow, n_overflow, spos, vin, ctx->cell_start,
       ctx->cell_end, ctx->counts, nullptr, nullptr, 0, n));
   MAFP_LAUNCH_CHECK(ctx);
   int rc = scan_i32_to_i64(ctx, ctx->counts, reinterpret_cast<long long *>(row_ptr), n, s);
@@ -679,16 +777,17 @@ static int build_neighbours_t(mafp_ctx *ctx, int64_t n, const void *pos_h, int64
                               ctx->d_status, ctx->d_grid));
   MAFP_TIMED(ctx, s, "k_nbr_expand",
              k_nbr_expand<T><<<sms * 16, kExpThreads, 0, s>>>(
-                 ctx->d_grid, ctx->ucell, ctx->n_ucell, vin, ctx->cell_start, ctx->cell_end,
+                 cg, ctx->ucell, ctx->n_ucell, vin, ctx->cell_start, ctx->cell_end,
                  ctx->nbr_mask, stride, reinterpret_cast<const long long *>(row_ptr), col,
                  cap_nnz, n));
   MAFP_TIMED(ctx, s, "k_nbr<T,true>(overflow cells)",
              k_nbr<T, true><<<nbr_blocks, kNbrThreads, kNbrSmemBytes, s>>>(
-      ctx->d_grid, ctx->ucell, ctx->overflow, n_overflow, spos, vin, ctx->cell_start,
+      cg, ctx->ucell, ctx->overflow, n_overflow, spos, vin, ctx->cell_start,
       ctx->cell_end, ctx->counts, reinterpret_cast<const long long *>(row_ptr), col, cap_nnz, n));
   MAFP_TIMED(ctx, s, "k_rowsort",
              k_rowsort<<<grid_for(n, kSortWarps, sms * 8), kSortWarps * 32, 0, s>>>(
-      reinterpret_cast<const long long *>(row_ptr), col, n, cap_nnz, ctx->d_status));
+      reinterpret_cast<const long long *>(row_ptr), col, n, cap_nnz, ctx->d_status,
+      ctx->d_grid));
   MAFP_LAUNCH_CHECK(ctx);
   return MAFP_OK;
 }
@@ -696,9 +795,24 @@ static int build_neighbours_t(mafp_ctx *ctx, int64_t n, const void *pos_h, int64
 int build_neighbours(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h,
                      int64_t *row_ptr, int32_t *col, int64_t cap_nnz, int64_t *nnz_dev,
                      int32_t *order, cudaStream_t s) {
+  MAFP_TIMED(ctx, s, "k_set_one_cloud", k_set_one_cloud<<<1, 1, 0, s>>>(ctx->one_cloud, n));
   if (dtype == MAFP_F64)
-    return build_neighbours_t<double>(ctx, n, pos_h, row_ptr, col, cap_nnz, nnz_dev, order, s);
-  return build_neighbours_t<float>(ctx, n, pos_h, row_ptr, col, cap_nnz, nnz_dev, order, s);
+    return build_neighbours_t<double>(ctx, n, 1, ctx->one_cloud, pos_h, row_ptr, col, cap_nnz,
+                                      nnz_dev, order, s);
+  return build_neighbours_t<float>(ctx, n, 1, ctx->one_cloud, pos_h, row_ptr, col, cap_nnz,
+                                   nnz_dev, order, s);
+}
+
+int build_neighbours_batched(mafp_ctx *ctx, int64_t n, int32_t dtype, int32_t nclouds,
+                             const int64_t *cloud_offset, const void *pos_h, int64_t *row_ptr,
+                             int32_t *col, int64_t cap_nnz, int64_t *nnz_dev, int32_t *order,
+                             cudaStream_t s) {
+  const long long *off = reinterpret_cast<const long long *>(cloud_offset);
+  if (dtype == MAFP_F64)
+    return build_neighbours_t<double>(ctx, n, nclouds, off, pos_h, row_ptr, col, cap_nnz,
+                                      nnz_dev, order, s);
+  return build_neighbours_t<float>(ctx, n, nclouds, off, pos_h, row_ptr, col, cap_nnz, nnz_dev,
+                                   order, s);
 }
 
 void init_kernel_attributes() {

@@ -23,7 +23,9 @@ __device__ __forceinline__ T warp_inclusive(T v) {
 // thread's exclusive prefix, *total gets the block total.
 template <typename T>
 __device__ __forceinline__ T block_exclusive(T v, T *total) {
-  __shared__ T warp_tot[32];
+  // [0, 32): per-warp totals, then per-warp exclusive offsets; [32]: block total
+  // (a slot of its own: with 32 warps, [31] is the last warp's offset)
+  __shared__ T warp_tot[33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   T inc = warp_inclusive(v);
   if (lane == 31) warp_tot[w] = inc;
@@ -32,11 +34,11 @@ __device__ __forceinline__ T block_exclusive(T v, T *total) {
     T t = lane < nw ? warp_tot[lane] : T(0);
     T ti = warp_inclusive(t);
     if (lane < nw) warp_tot[lane] = ti - t;
-    if (lane == nw - 1) warp_tot[31] = ti;
+    if (lane == nw - 1) warp_tot[32] = ti;
   }
   __syncthreads();
   T res = warp_tot[w] + inc - v;
-  *total = warp_tot[31];
+  *total = warp_tot[32];
   __syncthreads();
   return res;
 }

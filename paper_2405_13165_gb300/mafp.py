@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmafp.so")
 
 OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENOTIMPL, ENONFINITE = 0, -1, -2, -3, -4, -5, -6
+MAX_CLOUDS = 65536          # largest batch of mafp_build_neighbours_batched
 F32_REFINED, F32_PLAIN, F64 = 0, 1, 2
 MODEL_3D, MODEL_2D = 0, 1
 STENCIL_OK, STENCIL_DEFICIENT, STENCIL_FP64 = 0, 1, 2
@@ -82,6 +83,7 @@ def lib():
         L.mafp_get_status.argtypes = [p, p, p]
         L.mafp_reset_status.argtypes = [p, p]
         L.mafp_build_neighbours.argtypes = [p, i64, i32, p, p, p, i64, p, p, p]
+        L.mafp_build_neighbours_batched.argtypes = [p, i64, i32, i32, p, p, p, p, i64, p, p, p]
         L.mafp_classify_pca.argtypes = [p, i64, i32] + [p] * 17
         L.mafp_build_stencils.argtypes = [p, i64, i32, p, p, p, p, p, p, p, p, p]
         L.mafp_apply_ops.argtypes = [p, i64, i32, p, p, p, p, p, p]
@@ -94,7 +96,8 @@ def lib():
         L.mafp_profile.argtypes = [p, i32]
         L.mafp_profile_read.argtypes = [p, p, i32, p]
         for name in ("mafp_set_tuning", "mafp_get_tuning", "mafp_profile", "mafp_profile_read", "mafp_create", "mafp_destroy", "mafp_get_status", "mafp_reset_status",
-                     "mafp_build_neighbours", "mafp_classify_pca", "mafp_build_stencils",
+                     "mafp_build_neighbours", "mafp_build_neighbours_batched",
+                     "mafp_classify_pca", "mafp_build_stencils",
                      "mafp_apply_ops", "mafp_transpose_map", "mafp_apply_ops_backward",
                      "mafp_build_stencils_backward", "mafp_remap_switched"):
             getattr(L, name).restype = C.c_int
@@ -214,6 +217,23 @@ def build_neighbours(ctx: Context, pos_h, row_ptr, col, nnz=None, order=None, dt
     ctx.check(lib().mafp_build_neighbours(ctx.handle, n, dtype, _ptr(pos_h), _ptr(row_ptr),
                                           _ptr(col), col.numel(), _ptr(nnz), _ptr(order),
                                           _stream(stream)))
+
+
+def build_neighbours_batched(ctx: Context, cloud_offset, pos_h, row_ptr, col, nnz=None, order=None,
+                             dtype=F32_REFINED, stream=None):
+    """Eq. Nbd for clouds stored back to back, cloud b = [offset[b], offset[b+1])."""
+    n = pos_h.shape[0]
+    nb = cloud_offset.numel() - 1
+    _need(cloud_offset, "cloud_offset", torch.int64, nb + 1)
+    _need(pos_h, "pos_h", real_dtype(dtype), 4 * n)
+    _need(row_ptr, "row_ptr", torch.int64, n + 1)
+    _need(col, "col", torch.int32)
+    _need(nnz, "nnz", torch.int64, 1, allow_none=True)
+    _need(order, "order", torch.int32, n, allow_none=True)
+    ctx.check(lib().mafp_build_neighbours_batched(ctx.handle, n, dtype, nb, _ptr(cloud_offset),
+                                                  _ptr(pos_h), _ptr(row_ptr), _ptr(col),
+                                                  col.numel(), _ptr(nnz), _ptr(order),
+                                                  _stream(stream)))
 
 
 def neighbours(ctx: Context, pos_h, dtype=F32_REFINED, cap_nnz=None, order=False, stream=None):

@@ -12,8 +12,9 @@ CLOUD_KEYS = ("pos_h", "model", "ptype", "normal", "vp", "rho", "eta", "mass", "
               "h3d", "user", "last")
 
 
-def cloud_to_device(cloud, dtype=M.F32_REFINED, device="cuda", pin=False):
-    """Copy a generated Cloud to device tensors of the call's real type."""
+def cloud_to_device(cloud, dtype=M.F32_REFINED, device="cuda", pin=False, cloud_offset=None):
+    """Copy a generated Cloud to device tensors of the call's real type
+    (with the batch's int64 cloud offsets when given)."""
     rd = M.real_dtype(dtype)
     out = {}
     for k in CLOUD_KEYS:
@@ -24,6 +25,8 @@ def cloud_to_device(cloud, dtype=M.F32_REFINED, device="cuda", pin=False):
         out[k] = t.to(device, non_blocking=False)
     out["vol"] = torch.from_numpy(np.ascontiguousarray(cloud.vol)).to(rd).to(device)
     out["fields"] = out["vp"]
+    if cloud_offset is not None:
+        out["cloud_offset"] = torch.as_tensor(np.asarray(cloud_offset, np.int64)).to(device)
     return out
 
 
@@ -51,9 +54,17 @@ class Pipeline:
         self.out = z(cap_n, 4, 4)
 
     def neighbours(self, d, with_order=False, stream=None):
+        """Eq. Nbd; a cloud dict holding "cloud_offset" (int64 [B+1], device) is
+        a batch of independent clouds and takes the batched build."""
         n = d["pos_h"].shape[0]
-        M.build_neighbours(self.ctx, d["pos_h"], self.row_ptr[: n + 1], self.col, self.nnz,
-                           self.order[:n] if with_order else None, self.dtype, stream)
+        order = self.order[:n] if with_order else None
+        if d.get("cloud_offset") is not None:
+            M.build_neighbours_batched(self.ctx, d["cloud_offset"], d["pos_h"],
+                                       self.row_ptr[: n + 1], self.col, self.nnz, order,
+                                       self.dtype, stream)
+        else:
+            M.build_neighbours(self.ctx, d["pos_h"], self.row_ptr[: n + 1], self.col, self.nnz,
+                               order, self.dtype, stream)
 
     def classify(self, d, stream=None):
         n = d["pos_h"].shape[0]

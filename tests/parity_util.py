@@ -18,12 +18,13 @@ from paper_2405_13165_gb300.pipeline import Pipeline, cloud_to_device
 TOL = {M.F32_REFINED: 1e-4, M.F32_PLAIN: 2e-3, M.F64: 1e-10}
 
 
-def run_gpu(cloud, dtype, cap_nnz=None, ctx=None, stages=("nbr", "cls", "st", "ap")):
+def run_gpu(cloud, dtype, cap_nnz=None, ctx=None, stages=("nbr", "cls", "st", "ap"),
+            cloud_offset=None):
     n = cloud.n
     ctx = ctx or M.Context(max(n, 1))
     cap_nnz = cap_nnz or max(400 * n, 16)
     pipe = Pipeline(ctx, max(n, 1), cap_nnz, dtype)
-    d = cloud_to_device(cloud, dtype)
+    d = cloud_to_device(cloud, dtype, cloud_offset=cloud_offset)
     ctx.reset_status()
     if "nbr" in stages:
         pipe.neighbours(d, with_order=True)

@@ -85,6 +85,19 @@ def test_random_cloud_variable_h_unsorted(orc, seed, dtype):
                                rtol=1e-5 if dtype != M.F64 else 1e-12)
 
 
+def test_neighbours_past_one_scan_chunk(orc):
+    # 4.6M rows: more than 1024 scan tiles of 4096 rows, so the tile-sum scan
+    # takes several chunks and every warp of its block holds live tiles
+    c = C.random_cloud(4_600_000, seed=5, h_lo=0.018, h_hi=0.022, frac2d=0.0)
+    rp, col = orc.neighbours(c.pos_h)
+    ctx = M.Context(c.n)
+    t = torch.tensor(c.pos_h, device="cuda")
+    g_rp, g_col, _ = M.neighbours(ctx, t, cap_nnz=int(rp[-1]) + 1024)
+    np.testing.assert_array_equal(g_rp.cpu().numpy(), rp)
+    np.testing.assert_array_equal(g_col.cpu().numpy(), col)
+    ctx.close()
+
+
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_neighbour_edge_cases(orc, dtype):
     ctx = M.Context(64)
