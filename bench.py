@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="jet", choices=["jet", "batched"],
+                    help="jet: the 1M jet-on-plate step (default); batched: 256 independent "
+                         "cube-on-sheet clouds, forward pass replayed from a CUDA graph")
     ap.add_argument("--tuning", default=None,
                     help="fixed launch shapes 'g3d,g2d,gapply' instead of the autotuner")
     return ap.parse_args()
@@ -500,6 +503,114 @@ def bench_gpu(args):
         dist.destroy_process_group()
 
 
+def bench_batched(args):
+    """256 independent clouds in one batch (about 12M particles): neighbours,
+    detection, stencils and apply over the whole batch, one launch per stage,
+    the pass captured once in a CUDA graph and replayed.  Timed both eagerly
+    and by graph replay; L2 flushed before every timed pass."""
+    import torch
+
+    from paper_2405_13165_gb300 import autotune, clouds as C, mafp as M
+    from paper_2405_13165_gb300.pipeline import Pipeline, cloud_to_device
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    cloud, off = C.config_batched()
+    n, nb = cloud.n, len(off) - 1
+    dtype = M.F32_REFINED
+    ctx = M.Context(n)
+    d = cloud_to_device(cloud, dtype, dev, cloud_offset=off)
+    probe = torch.empty(1, dtype=torch.int32, device=dev)
+    rp = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    ctx.reset_status()
+    M.build_neighbours_batched(ctx, d["cloud_offset"], d["pos_h"], rp, probe)
+    nnz = int(rp[n].item())
+    ctx.reset_status()
+    pipe = Pipeline(ctx, n, nnz + 1024, dtype, dev)
+    tuned = autotune.tune(ctx, pipe, d, use_cache=False)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(max(args.warmup, 3)):
+            pipe.step(d, stream=s)
+    s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        pipe.step(d, stream=s)
+    launches = 0
+    ctx.profile(True)
+    with torch.cuda.stream(s):
+        pipe.step(d, stream=s)
+    s.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches = sum(v[0] for v in prof.values())
+
+    def timed(run):
+        tot = 0.0
+        with torch.cuda.stream(s):
+            for _ in range(args.steps):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                run()
+                e1.record(s)
+                s.synchronize()
+                tot += e0.elapsed_time(e1)
+        return tot / args.steps
+
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    ms_eager = timed(lambda: pipe.step(d, stream=s))
+    ms_graph = timed(graph.replay)
+    clocks = sampler.stop()
+    st = ctx.status()
+    if st["code"] != 0:
+        raise RuntimeError(f"device status after the batched passes: {st}")
+    hit = [v for k, v in prof.items() if k.startswith("k_apply<G=")]
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    roof = None
+    if hit:
+        ms = sum(v[1] for v in hit) / sum(v[0] for v in hit)
+        b = APPLY_BYTES_NNZ[4] * nnz + APPLY_BYTES_N[4] * n
+        ach = b / (ms * 1e-3) / 1e9
+        roof = {"kernel": "apply_ops", "bound": "hbm", "achieved": round(ach, 1),
+                "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+                "traffic": None, "launch_ms": round(ms, 4),
+                "peak_source": "of measured" if "hbm_gbs" in peaks else "of fallback"}
+    sizes = np.diff(off)
+    line = {
+        "metric": "particles/s for neighbour+PCA+stencil build+apply over a batch of clouds",
+        "value": round(n / (ms_graph * 1e-3), 1), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_graph, 4),
+        "ms_per_step_eager": round(ms_eager, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded cube-on-sheet clouds)",
+        "config": {"workload": f"batch of {nb} independent cube-on-sheet clouds, sizes log-uniform "
+                               f"2k-200k, film fraction U[0.1, 0.9], dx = 0.02 m",
+                   "n_particles": n, "nnz": nnz, "clouds": nb, "smallest": int(sizes.min()),
+                   "largest": int(sizes.max()), "n_2d": int((cloud.model == 1).sum()),
+                   "step": "batched neighbours, detection, stencils, apply (CUDA graph replay)",
+                   "l2": "flushed (256 MB write) before every timed pass",
+                   "parallelism": "single GPU"},
+        "roofline": roof, "tuning": tuned, "clocks": clocks,
+        "gpu_launches": int(launches * args.steps),
+        "kernel_profile_top": [{"kernel": k, "launches": v[0],
+                                "ms_per_launch": round(v[1] / v[0], 4)}
+                               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])[:12]],
+        "device_status": {k: st[k] for k in ("code", "n_fp64_stencil", "n_fp64_eigen",
+                                             "n_deficient", "n_near", "cells_identity")},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def bench_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -533,6 +644,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload == "batched":
+        bench_batched(args)
     else:
         bench_gpu(args)
 

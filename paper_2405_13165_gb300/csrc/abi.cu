@@ -147,7 +147,7 @@ int mafp_create(mafp_ctx **out, const mafp_params *params, int64_t cap_particles
       {(void **)&ctx->cell_base, sizeof(long long) * (kMaxClouds + 1)},
       {(void **)&ctx->cloud_id, sizeof(int32_t) * cap},
       {(void **)&ctx->one_cloud, sizeof(long long) * 2},
-      {(void **)&ctx->cloud_partial, sizeof(double) * (kMaxClouds + 1024) * 8},
+      {(void **)&ctx->cloud_partial, sizeof(double) * (kMaxClouds + 16384) * 8},
       {(void **)&ctx->remap_i64, sizeof(int64_t) * i64_len},
       {(void **)&ctx->remap_i32, sizeof(int32_t) * 3 * cap},
   };

@@ -73,7 +73,7 @@ struct mafp_ctx {
   long long *cell_base;      // [kMaxClouds + 1] first global cell of each cloud
   int32_t *cloud_id;         // [cap] cloud of every particle
   long long *one_cloud;      // [2] offsets of the single-cloud case
-  double *cloud_partial;     // [(kMaxClouds + 1024) * 8] bounding-box partials
+  double *cloud_partial;     // [(kMaxClouds + 16384) * 8] bounding-box partials
   int64_t *remap_i64;       // [3 * cap + 8]
   int32_t *remap_i32;       // [2 * cap]
   char err[512];

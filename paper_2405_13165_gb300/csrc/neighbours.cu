@@ -12,7 +12,8 @@ namespace mafp {
 
 // ---------------------------------------------------------------- grid set-up
 constexpr int kBoxThreads = 256;
-constexpr int kBoxBlocks = 1024;
+constexpr int kBoxBlocks = 16384;   // bounding-box blocks over all clouds
+constexpr int kBoxPartsMax = 1024;  // blocks of one cloud
 
 // ------------------------------------------------ several clouds, one grid each
 // Cloud b owns particles [off[b], off[b+1]) and cells [cell_base[b], cell_base[b+1])
@@ -31,7 +32,14 @@ __global__ void k_set_one_cloud(long long *off, int64_t n) {
 }
 
 // Block (b, part) reduces part `part` of cloud b: min / max of x, y, z, max h,
-// count of non-finite entries; also records each particle's cloud.
+// count of non-finite entries; also records each particle's cloud.  Min and
+// max are exact in the input's own type, so they are taken in it and widened
+// once per block.
+template <typename T>
+__device__ __forceinline__ T lo_of(T a, T b) { return b < a ? b : a; }
+template <typename T>
+__device__ __forceinline__ T hi_of(T a, T b) { return b > a ? b : a; }
+
 template <typename T>
 __global__ void __launch_bounds__(kBoxThreads) k_cloud_bbox(const vec4_t<T> *pos, int64_t n,
                                                             const long long *off, int nb,
@@ -41,21 +49,67 @@ __global__ void __launch_bounds__(kBoxThreads) k_cloud_bbox(const vec4_t<T> *pos
   // offsets are checked in k_cloud_grid; clamping keeps every access in [0, n)
   const long long lo = max(0LL, min(off[b], (long long)n));
   const long long hi = max(lo, min(off[b + 1], (long long)n));
-  double v[8] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0, 0.0};
+  const T inf = T(INFINITY);
+  T v[7] = {inf, inf, inf, -inf, -inf, -inf, T(0)};
+  int bad = 0;
   for (long long i = lo + (long long)part * blockDim.x + threadIdx.x; i < hi;
        i += (long long)parts * blockDim.x) {
     cloud_id[i] = b;
-    vec4_t<T> p = ld4(pos + i);
-    bool ok = isfinite((double)p.x) && isfinite((double)p.y) && isfinite((double)p.z) &&
-              isfinite((double)p.w) && p.w > T(0);
+    const vec4_t<T> p = ld4(pos + i);
+    const bool ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w) && p.w > T(0);
     if (!ok) {
-      v[7] += 1.0;
+      ++bad;
       continue;
     }
-    v[0] = fmin(v[0], (double)p.x); v[1] = fmin(v[1], (double)p.y); v[2] = fmin(v[2], (double)p.z);
-    v[3] = fmax(v[3], (double)p.x); v[4] = fmax(v[4], (double)p.y); v[5] = fmax(v[5], (double)p.z);
-    v[6] = fmax(v[6], (double)p.w);
+    v[0] = lo_of(v[0], p.x); v[1] = lo_of(v[1], p.y); v[2] = lo_of(v[2], p.z);
+    v[3] = hi_of(v[3], p.x); v[4] = hi_of(v[4], p.y); v[5] = hi_of(v[5], p.z);
+    v[6] = hi_of(v[6], p.w);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = lo_of(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+#pragma unroll
+    for (int k = 3; k < 7; ++k) v[k] = hi_of(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  __shared__ T red[kBoxThreads / 32][7];
+  __shared__ int red_bad[kBoxThreads / 32];
+  if ((threadIdx.x & 31) == 0) {
+    for (int k = 0; k < 7; ++k) red[threadIdx.x >> 5][k] = v[k];
+    red_bad[threadIdx.x >> 5] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int k = threadIdx.x;
+    double a;
+    if (k < 7) {
+      T r = red[0][k];
+      for (int w = 1; w < kBoxThreads / 32; ++w)
+        r = k < 3 ? lo_of(r, red[w][k]) : hi_of(r, red[w][k]);
+      a = (double)r;
+    } else {
+      int s = 0;
+      for (int w = 0; w < kBoxThreads / 32; ++w) s += red_bad[w];
+      a = (double)s;
+    }
+    partial[(long long)blockIdx.x * 8 + k] = a;
+  }
+}
+
+// One warp per cloud folds the cloud's `parts` partials (lanes over parts,
+// then shuffles) and leaves the cloud's box in its first partial slot.
+__global__ void __launch_bounds__(kBoxThreads) k_cloud_fold(double *partial, int nb, int parts) {
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x * (kBoxThreads / 32) + (threadIdx.x >> 5);
+  if (b >= nb) return;
+  double v[8] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0, 0.0};
+  double *pb = partial + (long long)b * parts * 8;
+  for (int q = lane; q < parts; q += 32)
+    for (int k = 0; k < 8; ++k) {
+      const double a = pb[q * 8 + k];
+      v[k] = k < 3 ? fmin(v[k], a) : (k < 7 ? fmax(v[k], a) : v[k] + a);
+    }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -64,17 +118,9 @@ __global__ void __launch_bounds__(kBoxThreads) k_cloud_bbox(const vec4_t<T> *pos
     for (int k = 3; k < 7; ++k) v[k] = fmax(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
     v[7] += __shfl_xor_sync(0xffffffffu, v[7], o);
   }
-  __shared__ double red[kBoxThreads / 32][8];
-  if ((threadIdx.x & 31) == 0)
-    for (int k = 0; k < 8; ++k) red[threadIdx.x >> 5][k] = v[k];
-  __syncthreads();
-  if (threadIdx.x < 8) {
-    const int k = threadIdx.x;
-    double a = red[0][k];
-    for (int w = 1; w < kBoxThreads / 32; ++w)
-      a = k < 3 ? fmin(a, red[w][k]) : (k < 7 ? fmax(a, red[w][k]) : a + red[w][k]);
-    partial[(long long)blockIdx.x * 8 + k] = a;
-  }
+  __syncwarp();
+  if (lane == 0)
+    for (int k = 0; k < 8; ++k) pb[k] = v[k];
 }
 
 // Cells of cloud b at edge c (>= max h of the cloud); 0 for an empty cloud.
@@ -92,11 +138,11 @@ __device__ double cloud_cells(const double v[8], double c, int dim[3]) {
   return cells;
 }
 
-// One block: per-cloud bounding boxes and grids, the global cell numbering
+// One block: per-cloud grids from the folded boxes, the global cell numbering
 // (exclusive scan of the clouds' cell counts) and the all-clouds flag.  The cell
 // edge of every cloud starts strictly above its max h (so S_i lies in the 27
 // cells around i's cell) and grows uniformly when the total exceeds cap_cells.
-__global__ void __launch_bounds__(kBoxThreads) k_cloud_grid(const double *partial,
+__global__ void __launch_bounds__(kBoxThreads) k_cloud_grid(double *partial,
                                                             const long long *off, int64_t n,
                                                             int nb, int parts, GridDev *grids,
                                                             long long *cell_base, GridDev *all,
@@ -123,20 +169,8 @@ __global__ void __launch_bounds__(kBoxThreads) k_cloud_grid(const double *partia
     return;
   }
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    double v[8] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0, 0.0};
-    for (int q = 0; q < parts; ++q)
-      for (int k = 0; k < 8; ++k) {
-        const double a = partial[((long long)b * parts + q) * 8 + k];
-        v[k] = k < 3 ? fmin(v[k], a) : (k < 7 ? fmax(v[k], a) : v[k] + a);
-      }
-    if (v[7] > 0.0) atomicAdd(&s_nonfinite, v[7]);
-    GridDev &g = grids[b];
-    for (int a = 0; a < 3; ++a) g.lo[a] = v[a] < INFINITY ? v[a] : 0.0;
-    g.hmax = v[6];
-    g.c = v[6] * (1.0 + 1e-6);
-    g.inv_c = v[6] > 0.0 ? 1.0 / g.c : 1.0;
-    // stash the box in the grid record until the edge is final
-    g.dim[0] = g.dim[1] = g.dim[2] = 1;
+    const double bad = partial[(long long)b * parts * 8 + 7];
+    if (bad > 0.0) atomicAdd(&s_nonfinite, bad);
   }
   __syncthreads();
   if (s_nonfinite > 0.0) {
@@ -151,16 +185,14 @@ __global__ void __launch_bounds__(kBoxThreads) k_cloud_grid(const double *partia
     if (threadIdx.x == 0) s_cells = 0.0;
     __syncthreads();
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      double v[8] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0, 0.0};
-      for (int q = 0; q < parts; ++q)
-        for (int k = 0; k < 7; ++k) {
-          const double a = partial[((long long)b * parts + q) * 8 + k];
-          v[k] = k < 3 ? fmin(v[k], a) : fmax(v[k], a);
-        }
+      double v[8];
+      for (int k = 0; k < 8; ++k) v[k] = partial[(long long)b * parts * 8 + k];
       int dim[3];
       const double c = v[6] * (1.0 + 1e-6) * s_scale;
       const double cells = cloud_cells(v, c, dim);
       GridDev &g = grids[b];
+      for (int a = 0; a < 3; ++a) g.lo[a] = v[a] < INFINITY ? v[a] : 0.0;
+      g.hmax = v[6];
       g.c = c;
       g.inv_c = v[6] > 0.0 ? 1.0 / c : 1.0;
       for (int a = 0; a < 3; ++a) g.dim[a] = dim[a];
@@ -715,11 +747,14 @@ static int build_neighbours_t(mafp_ctx *ctx, int64_t n, int nb, const long long 
   using V = vec4_t<T>;
   const V *pos = reinterpret_cast<const V *>(pos_h);
   const int sms = sm_count();
-  const int parts = std::max(1, std::min(kBoxBlocks / std::max(nb, 1), 64));
+  const int parts = std::max(1, std::min(kBoxBlocks / std::max(nb, 1), kBoxPartsMax));
   MAFP_TIMED(ctx, s, "k_cloud_bbox",
              k_cloud_bbox<T><<<nb * parts, kBoxThreads, 0, s>>>(pos, n, cloud_off, nb, parts,
                                                                  ctx->cloud_partial,
                                                                  ctx->cloud_id));
+  MAFP_TIMED(ctx, s, "k_cloud_fold",
+             k_cloud_fold<<<(nb + kBoxThreads / 32 - 1) / (kBoxThreads / 32), kBoxThreads, 0, s>>>(
+                 ctx->cloud_partial, nb, parts));
   MAFP_TIMED(ctx, s, "k_cloud_grid",
              k_cloud_grid<<<1, kBoxThreads, 0, s>>>(ctx->cloud_partial, cloud_off, n, nb, parts,
                                                     ctx->d_grids,

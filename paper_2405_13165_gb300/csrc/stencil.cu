@@ -14,6 +14,9 @@ namespace mafp {
 
 __global__ void k_reset_queue(DevStatus *st) { st->fallback_count = 0; }
 
+constexpr int kGatherU = 4;   // neighbours a lane gathers ahead of use
+constexpr int kGatherR = 2;   // the same in the refinement pass (more live registers)
+
 // Process particle i with a group of G lanes.  Returns (through *result)
 //  0 = written, 1 = deficient (zeros written), 2 = queued for FP64.
 template <typename TS, typename C, int M, int G, bool REFINE, bool QUEUE>
@@ -45,18 +48,23 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
 #pragma unroll
   for (int k = 0; k < VA; ++k) A[k] = C(0);
   int cnt = 0;
-  for (long long e = b + lane; e < e1; e += G) {
-    const int j = col[e];
-    if (model[j] != mi) continue;
-    C p[M];
-    const C w = basis_at<M, C>(xi, ld4(pos + j), hinv, t1, t2, sp, p);
+  for (long long e0 = b + lane; e0 < e1; e0 += kGatherU * G) {
+    V xs[kGatherU];
+    bool oks[kGatherU];
+    gather_row<kGatherU, G>(e0, e1, i, mi, col, pos, model, xs, oks);
 #pragma unroll
-    for (int r = 0; r < M; ++r) {
-      const C wp = w * p[r];
+    for (int u = 0; u < kGatherU; ++u) {
+      C p[M];
+      C w = basis_at<M, C>(xi, xs[u], hinv, t1, t2, sp, p);
+      w = oks[u] ? w : C(0);   // other model / past the row end: contributes exact zeros
+      cnt += oks[u] ? 1 : 0;
 #pragma unroll
-      for (int c = 0; c <= r; ++c) A[pk(r, c)] += wp * p[c];
+      for (int r = 0; r < M; ++r) {
+        const C wp = w * p[r];
+#pragma unroll
+        for (int c = 0; c <= r; ++c) A[pk(r, c)] += wp * p[c];
+      }
     }
-    ++cnt;
   }
   cnt = group_sum<G>(cnt);
   reduce_scatter<G, VA>(A);
@@ -105,19 +113,24 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
     C R[VR];
 #pragma unroll
     for (int k = 0; k < VR; ++k) R[k] = C(0);
-    for (long long e = b + lane; e < e1; e += G) {
-      const int j = col[e];
-      if (model[j] != mi) continue;
-      C p[M];
-      const C w = basis_at<M, C>(xi, ld4(pos + j), hinv, t1, t2, sp, p);
+    for (long long e0 = b + lane; e0 < e1; e0 += kGatherR * G) {
+      V xs[kGatherR];
+      bool oks[kGatherR];
+      gather_row<kGatherR, G>(e0, e1, i, mi, col, pos, model, xs, oks);
 #pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        C s = 0;
+      for (int u = 0; u < kGatherR; ++u) {
+        C p[M];
+        C w = basis_at<M, C>(xi, xs[u], hinv, t1, t2, sp, p);
+        w = oks[u] ? w : C(0);
 #pragma unroll
-        for (int r = 0; r < M; ++r) s += p[r] * lam[k][r];
-        const C c = w * s;
+        for (int k = 0; k < NR; ++k) {
+          C s = 0;
 #pragma unroll
-        for (int r = 0; r < M; ++r) R[k * M + r] += c * p[r];
+          for (int r = 0; r < M; ++r) s += p[r] * lam[k][r];
+          const C c = w * s;
+#pragma unroll
+          for (int r = 0; r < M; ++r) R[k * M + r] += c * p[r];
+        }
       }
     }
     reduce_scatter<G, VR>(R);
@@ -137,12 +150,18 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
   }
   // ---- coefficients
   const C h2inv = hinv * hinv;
-  for (long long e = b + lane; e < e1; e += G) {
-    const int j = col[e];
+  for (long long e0 = b + lane; e0 < e1; e0 += kGatherU * G) {
+    V xs[kGatherU];
+    bool oks[kGatherU];
+    gather_row<kGatherU, G>(e0, e1, i, mi, col, pos, model, xs, oks);
+#pragma unroll
+    for (int u = 0; u < kGatherU; ++u) {
+    const long long e = e0 + (long long)u * G;
+    if (e >= e1) break;
     vec4_t<TS> out = mk4<TS>(0, 0, 0, 0);
-    if (model[j] == mi) {
+    if (oks[u]) {
       C p[M];
-      const C w = basis_at<M, C>(xi, ld4(pos + j), hinv, t1, t2, sp, p);
+      const C w = basis_at<M, C>(xi, xs[u], hinv, t1, t2, sp, p);
       C c[NR];
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
@@ -161,6 +180,7 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
       }
     }
     st4(coef + e, out);
+    }
   }
   *result = 0;
   *cond_out = (float)cond;

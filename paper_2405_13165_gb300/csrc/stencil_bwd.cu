@@ -17,7 +17,23 @@
 
 namespace mafp {
 
-template <typename T> __device__ __forceinline__ void atomic_add_r(T *p, T v) { atomicAdd(p, v); }
+// dL/dx of one particle into its 4-wide gpos record: one vector atomic for
+// FP32 (16-byte aligned records), three scalar ones for FP64.
+template <typename T>
+__device__ __forceinline__ void add_xyz(T *p, T x, T y, T z);
+template <>
+__device__ __forceinline__ void add_xyz<float>(float *p, float x, float y, float z) {
+  atomicAdd(reinterpret_cast<float4 *>(p), make_float4(x, y, z, 0.0f));
+}
+template <>
+__device__ __forceinline__ void add_xyz<double>(double *p, double x, double y, double z) {
+  atomicAdd(p, x);
+  atomicAdd(p + 1, y);
+  atomicAdd(p + 2, z);
+}
+
+// neighbours a lane gathers ahead of use in the moment, lbar and gradient passes
+constexpr int kGradGatherA = 4, kGradGatherB = 2, kGradGatherC = 2;
 
 // Returns 0 done, 1 no gradient (deficient), 2 queued for the FP64 redo.
 template <typename TS, typename C, int M, int G, bool QUEUE>
@@ -48,18 +64,23 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
 #pragma unroll
   for (int k = 0; k < VA; ++k) A[k] = C(0);
   int cnt = 0;
-  for (long long e = b + lane; e < e1; e += G) {
-    const int j = col[e];
-    if (model[j] != mi) continue;
-    C p[M];
-    const C w = basis_at<M, C>(xi, ld4(pos + j), hinv, t1, t2, sp, p);
+  for (long long e0 = b + lane; e0 < e1; e0 += kGradGatherA * G) {
+    V xs[kGradGatherA];
+    bool oks[kGradGatherA];
+    gather_row<kGradGatherA, G>(e0, e1, i, mi, col, pos, model, xs, oks);
 #pragma unroll
-    for (int r = 0; r < M; ++r) {
-      const C wp = w * p[r];
+    for (int u = 0; u < kGradGatherA; ++u) {
+      C p[M];
+      C w = basis_at<M, C>(xi, xs[u], hinv, t1, t2, sp, p);
+      w = oks[u] ? w : C(0);   // other model / past the row end: contributes exact zeros
+      cnt += oks[u] ? 1 : 0;
 #pragma unroll
-      for (int c = 0; c <= r; ++c) A[pk(r, c)] += wp * p[c];
+      for (int r = 0; r < M; ++r) {
+        const C wp = w * p[r];
+#pragma unroll
+        for (int c = 0; c <= r; ++c) A[pk(r, c)] += wp * p[c];
+      }
     }
-    ++cnt;
   }
   cnt = group_sum<G>(cnt);
   reduce_scatter<G, VA>(A);
@@ -122,17 +143,23 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
     C R[VR];
 #pragma unroll
     for (int k = 0; k < VR; ++k) R[k] = C(0);
-    for (long long e = b + lane; e < e1; e += G) {
-      const int j = col[e];
-      if (model[j] != mi) continue;
-      C p[M], gb[NR];
-      const C w = basis_at<M, C>(xi, ld4(pos + j), hinv, t1, t2, sp, p);
-      gbar(ld4(fields + j), gb);
+    for (long long e0 = b + lane; e0 < e1; e0 += kGradGatherB * G) {
+      V xs[kGradGatherB], fs[kGradGatherB];
+      int js[kGradGatherB];
+      bool oks[kGradGatherB];
+      gather_row_f<kGradGatherB, G>(e0, e1, i, mi, col, pos, model, fields, xs, fs, js, oks);
 #pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        const C gw = gb[k] * w;
+      for (int u = 0; u < kGradGatherB; ++u) {
+        C p[M], gb[NR];
+        C w = basis_at<M, C>(xi, xs[u], hinv, t1, t2, sp, p);
+        w = oks[u] ? w : C(0);
+        gbar(fs[u], gb);
 #pragma unroll
-        for (int r = 0; r < M; ++r) R[k * M + r] += gw * p[r];
+        for (int k = 0; k < NR; ++k) {
+          const C gw = gb[k] * w;
+#pragma unroll
+          for (int r = 0; r < M; ++r) R[k * M + r] += gw * p[r];
+        }
       }
     }
     reduce_scatter<G, VR>(R);
@@ -152,16 +179,23 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
   // ---- pass 2: wbar, pbar -> dL/dx_j (scattered) and -sum for x_i
   const C a2 = C(-2) * sp.alpha * sp.inv_den;  // W'(s)/s = a2 exp(-alpha s^2)
   C acc_i[3] = {0, 0, 0};
-  for (long long e = b + lane; e < e1; e += G) {
-    const int j = col[e];
-    if (model[j] != mi || j == i) continue;
-    const V xj = ld4(pos + j);
+  for (long long e0 = b + lane; e0 < e1; e0 += kGradGatherC * G) {
+    V xs[kGradGatherC], fs[kGradGatherC];
+    int js[kGradGatherC];
+    bool oks[kGradGatherC];
+    gather_row_f<kGradGatherC, G>(e0, e1, i, mi, col, pos, model, fields, xs, fs, js, oks);
+#pragma unroll
+    for (int u = 0; u < kGradGatherC; ++u) {
+    const int j = js[u];
+    if (!oks[u] || j == i) continue;
+    const V xj = xs[u];
     C p[M], gb[NR];
     const C w = basis_at<M, C>(xi, xj, hinv, t1, t2, sp, p);
-    gbar(ld4(fields + j), gb);
+    gbar(fs[u], gb);
     const C dx = C(xj.x) - C(xi.x), dy = C(xj.y) - C(xi.y), dz = C(xj.z) - C(xi.z);
     const C s2 = ((dx * dx + dy * dy) + dz * dz) * (hinv * hinv);
     const C dws = s2 <= C(1) ? a2 * exp(-sp.alpha * s2) : C(0);
+    // pbar = w sum_k ((gbar_k - t_k) lambda_k - s_k mu_k), the factor w applied last
     C wbar = 0, pbar[M];
 #pragma unroll
     for (int r = 0; r < M; ++r) pbar[r] = 0;
@@ -173,10 +207,13 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
         s += p[r] * lam[k][r];
         t += p[r] * mu[k][r];
       }
-      wbar += (gb[k] - t) * s;
+      const C a = gb[k] - t;
+      wbar += a * s;
 #pragma unroll
-      for (int r = 0; r < M; ++r) pbar[r] += w * (gb[k] * lam[k][r] - s * mu[k][r] - t * lam[k][r]);
+      for (int r = 0; r < M; ++r) pbar[r] += a * lam[k][r] - s * mu[k][r];
     }
+#pragma unroll
+    for (int r = 0; r < M; ++r) pbar[r] *= w;
     const C wq = dws * wbar;
     C d[3];
     if constexpr (M == 10) {
@@ -195,23 +232,19 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
       d[1] = (xb * t1[1] + eb * t2[1]) * hinv + wq * dy * hinv * hinv;
       d[2] = (xb * t1[2] + eb * t2[2]) * hinv + wq * dz * hinv * hinv;
     }
+    add_xyz<TS>(gpos + 4 * (int64_t)j, TS(d[0]), TS(d[1]), TS(d[2]));
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      atomic_add_r<TS>(gpos + 4 * (int64_t)j + a, TS(d[a]));
-      acc_i[a] -= d[a];
+    for (int a = 0; a < 3; ++a) acc_i[a] -= d[a];
     }
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) acc_i[a] = group_sum<G>(acc_i[a]);
-  if (lane == 0) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) atomic_add_r<TS>(gpos + 4 * i + a, TS(acc_i[a]));
-  }
+  if (lane == 0) add_xyz<TS>(gpos + 4 * i, TS(acc_i[0]), TS(acc_i[1]), TS(acc_i[2]));
   return 0;
 }
 
 template <typename TS, typename C, int M, int G, bool QUEUE>
-__global__ void __launch_bounds__(kStThreads) k_stencil_grad(
+__global__ void __launch_bounds__(kStThreads, sizeof(C) == 4 ? (M == 10 ? 3 : 4) : 1) k_stencil_grad(
     int64_t n, const vec4_t<TS> *pos, const uint8_t *model, const vec4_t<TS> *frame,
     const long long *row_ptr, const int32_t *col, const vec4_t<TS> *fields,
     const vec4_t<TS> *gout, TS *gpos, StParams<C> sp, DevStatus *st, int32_t *queue) {

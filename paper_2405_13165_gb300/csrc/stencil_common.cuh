@@ -140,6 +140,52 @@ __device__ __forceinline__ void chol_solve_s(const C *L, const C (&invd)[M], con
   }
 }
 
+// U neighbours of one lane (entries e0, e0 + G, ..., e0 + (U-1) G of the row),
+// gathered before any of them is used so that their loads are in flight
+// together.  Slots past the row end load particle i itself and are marked
+// invalid, as are neighbours of the other model.
+template <int U, int G, typename V>
+__device__ __forceinline__ void gather_row(long long e0, long long e1, int64_t i, uint8_t mi,
+                                           const int32_t *col, const V *pos,
+                                           const uint8_t *model, V (&x)[U], bool (&ok)[U]) {
+  int j[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const long long e = e0 + (long long)u * G;
+    j[u] = e < e1 ? col[e] : (int)i;
+  }
+  uint8_t m[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    x[u] = ld4(pos + j[u]);
+    m[u] = model[j[u]];
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) ok[u] = (e0 + (long long)u * G < e1) && m[u] == mi;
+}
+
+// The same, also gathering a per-particle field record of every neighbour.
+template <int U, int G, typename V>
+__device__ __forceinline__ void gather_row_f(long long e0, long long e1, int64_t i, uint8_t mi,
+                                             const int32_t *col, const V *pos,
+                                             const uint8_t *model, const V *fld, V (&x)[U],
+                                             V (&f)[U], int (&j)[U], bool (&ok)[U]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const long long e = e0 + (long long)u * G;
+    j[u] = e < e1 ? col[e] : (int)i;
+  }
+  uint8_t m[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    x[u] = ld4(pos + j[u]);
+    f[u] = ld4(fld + j[u]);
+    m[u] = model[j[u]];
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) ok[u] = (e0 + (long long)u * G < e1) && m[u] == mi;
+}
+
 template <int M, int G>
 struct StSmem {
   static constexpr int NA = Basis<M>::NA, NR = Basis<M>::NR;
