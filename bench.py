@@ -3,7 +3,7 @@
 
 One step = one pass of the whole path over the cloud, through the C ABI:
 build_neighbours -> classify_pca (+ smoothing) -> remap_switched ->
-build_stencils -> apply_ops -> transpose_map -> apply_ops_backward ->
+build_stencils -> apply_ops -> apply_ops_backward (scatter form) ->
 build_stencils_backward.  Workload: the jet-impingement cloud (vertical 3D
 cylinder r = 0.05 m, h = 0.5 m on a plate with a radial one-layer film disc
 r = 1 m), dx bisected to 1M particles, h = 3.5 dx, jitter +-0.1 dx, stored in
@@ -197,7 +197,6 @@ def bench_gpu(args):
     ctx.reset_status()
     cap_nnz = nnz + 1024
     pipe = Pipeline(ctx, n, cap_nnz, dtype, dev)
-    tloc = torch.empty(cap_nnz, dtype=torch.int16, device=dev)
     gout = torch.empty(n, 4, 4, dtype=torch.float32, device=dev)
     gfields = torch.empty(n, 4, dtype=torch.float32, device=dev)
     gpos = torch.empty(n, 4, dtype=torch.float32, device=dev)
@@ -233,9 +232,8 @@ def bench_gpu(args):
         mark()
         pipe.apply(d)
         mark()
-        M.transpose_map(ctx, pipe.row_ptr[: n + 1], pipe.col, tloc)
         gout.copy_(pipe.out[:n])
-        M.apply_ops_backward(ctx, pipe.row_ptr[: n + 1], pipe.col, tloc, pipe.coef, gout,
+        M.apply_ops_backward(ctx, pipe.row_ptr[: n + 1], pipe.col, None, pipe.coef, gout,
                              gfields, dtype)
         if have_bwd:
             try:

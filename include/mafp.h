@@ -254,8 +254,11 @@ int mafp_transpose_map(mafp_ctx *ctx, int64_t n, const int64_t *row_ptr, const i
 /* mafp_apply_ops_backward -- exact adjoint of mafp_apply_ops w.r.t. the
  * field values:  gfields[j][f] = sum_{i in S_j} sum_op coef_ij^op gout[4i+f][op]
  *                               - sum_op (sum_k coef_jk^op) gout[4j+f][op],
- * gathered through tloc (deterministic order; the second term vanishes for
- * stencils that annihilate constants).  gout x4 [4n], gfields x4 [n]. */
+ * (the second term vanishes for stencils that annihilate constants).
+ * tloc from mafp_transpose_map: every gfields[j] is gathered from row j in a
+ * fixed order (deterministic).  tloc NULL: rows scatter into gfields with
+ * atomic adds (no map needed; summation order unspecified, gfields zeroed by
+ * the call).  gout x4 [4n], gfields x4 [n]. */
 int mafp_apply_ops_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const int64_t *row_ptr,
                             const int32_t *col, const uint16_t *tloc, const void *coef,
                             const void *gout, void *gfields, void *stream);

@@ -4,7 +4,7 @@
 applied operators out[i, f] = (d_x, d_y, d_z, Lap) of the four fields
 (Eq. GFDM_Definition with the stencils of Sec. 2.3).  Its backward runs the
 library's hand-written kernels: the exact transpose of apply_ops for the
-fields and the stencil adjoint (moment matrix and Cholesky recomputed per
+fields (scattered with atomic adds) and the stencil adjoint (moment matrix and Cholesky recomputed per
 particle) for the positions.  Neighbour sets, models and film tangent frames
 are inputs held fixed; the smoothing length column of pos_h gets no gradient.
 """
@@ -41,10 +41,9 @@ class _GfdmOperators(torch.autograd.Function):
         n = pos_h.shape[0]
         gpos = gfields = None
         if fctx.needs_input_grad[1]:
-            tloc = torch.empty(max(col.numel(), 1), dtype=torch.int16, device=pos_h.device)
-            M.transpose_map(mctx, row_ptr, col, tloc)
+            # scatter form of the adjoint: no transpose map for a one-off backward
             gfields = torch.empty_like(fields)
-            M.apply_ops_backward(mctx, row_ptr, col, tloc, coef, gout, gfields, dtype)
+            M.apply_ops_backward(mctx, row_ptr, col, None, coef, gout, gfields, dtype)
         if fctx.needs_input_grad[0]:
             gpos = torch.empty_like(pos_h)
             M.build_stencils_backward(mctx, pos_h.detach(), model, frame, row_ptr, col,

@@ -344,7 +344,7 @@ int mafp_apply_ops_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const int64
   if ((rc = check_dtype(ctx, dtype))) return rc;
   if (n < 0) return fail(ctx, MAFP_EINVAL, "negative particle count");
   if (n == 0) return MAFP_OK;
-  REQUIRE(row_ptr); REQUIRE(col); REQUIRE(tloc); REQUIRE(coef); REQUIRE(gout); REQUIRE(gfields);
+  REQUIRE(row_ptr); REQUIRE(col); REQUIRE(coef); REQUIRE(gout); REQUIRE(gfields);
   if (ensure_device(ctx)) return MAFP_ECUDA;
   return apply_ops_backward(ctx, n, dtype, row_ptr, col, tloc, coef, gout, gfields,
                             (cudaStream_t)stream);

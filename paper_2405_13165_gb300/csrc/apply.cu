@@ -1,6 +1,7 @@
 // apply.cu -- stencil application of Eq. GFDM_Definition as a ragged gather-SpMV
-// (four fields x four operators per row) and its transpose through the
-// symmetric-structure map (gather, no atomics).
+// (four fields x four operators per row) and its transpose, either gathered
+// through the symmetric-structure map (deterministic) or scattered with
+// atomic adds (no map needed).
 #include "internal.cuh"
 
 namespace mafp {
@@ -124,6 +125,63 @@ __global__ void __launch_bounds__(kApThreads) k_apply_T(int64_t n, const long lo
   }
 }
 
+// The same adjoint scattered from the rows: row i adds coef[e] . gout[i][f] to
+// gfields[col[e]] (one vector atomic per entry in FP32) and subtracts its own
+// row sums once; needs no transpose map, sums in an unspecified order.
+template <typename T>
+__device__ __forceinline__ void add4(vec4_t<T> *p, T x, T y, T z, T w);
+template <>
+__device__ __forceinline__ void add4<float>(float4 *p, float x, float y, float z, float w) {
+  atomicAdd(p, make_float4(x, y, z, w));
+}
+template <>
+__device__ __forceinline__ void add4<double>(double4_16a *p, double x, double y, double z,
+                                             double w) {
+  double *q = reinterpret_cast<double *>(p);
+  atomicAdd(q, x);
+  atomicAdd(q + 1, y);
+  atomicAdd(q + 2, z);
+  atomicAdd(q + 3, w);
+}
+
+template <typename T, int G>
+__global__ void __launch_bounds__(kApThreads) k_apply_T_scatter(int64_t n,
+                                                                const long long *row_ptr,
+                                                                const int32_t *col,
+                                                                const vec4_t<T> *coef,
+                                                                const vec4_t<T> *gout,
+                                                                vec4_t<T> *gfields) {
+  using V = vec4_t<T>;
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t i = gid; i < n; i += ngroups) {
+    const long long b = row_ptr[i], e1 = row_ptr[i + 1];
+    V g[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) g[f] = ld4(gout + 4 * i + f);
+    T cs[4] = {0, 0, 0, 0};
+    for (long long e = b + lane; e < e1; e += G) {
+      const int j = __ldg(col + e);
+      const V c = ld4(coef + e);
+      cs[0] += c.x; cs[1] += c.y; cs[2] += c.z; cs[3] += c.w;
+      T v[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) v[f] = c.x * g[f].x + c.y * g[f].y + c.z * g[f].z + c.w * g[f].w;
+      add4<T>(gfields + j, v[0], v[1], v[2], v[3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cs[k] = group_sum<G>(cs[k]);
+    if (lane == 0) {
+      T v[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        v[f] = -(cs[0] * g[f].x + cs[1] * g[f].y + cs[2] * g[f].z + cs[3] * g[f].w);
+      add4<T>(gfields + i, v[0], v[1], v[2], v[3]);
+    }
+  }
+}
+
 template <typename T>
 static void launch_apply(mafp_ctx *ctx, cudaStream_t s, int64_t n, const long long *rp,
                          const int32_t *col, const void *coef, const void *fields, void *out) {
@@ -143,7 +201,7 @@ static void launch_apply(mafp_ctx *ctx, cudaStream_t s, int64_t n, const long lo
 }
 
 template <typename T>
-static void launch_apply_T(mafp_ctx *ctx, cudaStream_t s, int64_t n, const long long *rp,
+static int launch_apply_T(mafp_ctx *ctx, cudaStream_t s, int64_t n, const long long *rp,
                            const int32_t *col, const uint16_t *tloc, const void *coef,
                            const void *gout, void *gfields) {
   using V = vec4_t<T>;
@@ -151,6 +209,17 @@ static void launch_apply_T(mafp_ctx *ctx, cudaStream_t s, int64_t n, const long 
   const int blocks = grid_for(n * G, kApThreads, sm_count() * 64);
   const V *c = (const V *)coef, *g = (const V *)gout;
   V *o = (V *)gfields;
+  if (!tloc) {
+    MAFP_CUDA_TRY(ctx, cudaMemsetAsync(gfields, 0, (size_t)n * sizeof(V), s));
+    if (G == 4) {
+      MAFP_TIMED(ctx, s, "k_apply_T_scatter<G=4>", k_apply_T_scatter<T, 4><<<blocks, kApThreads, 0, s>>>(n, rp, col, c, g, o));
+    } else if (G == 16) {
+      MAFP_TIMED(ctx, s, "k_apply_T_scatter<G=16>", k_apply_T_scatter<T, 16><<<blocks, kApThreads, 0, s>>>(n, rp, col, c, g, o));
+    } else {
+      MAFP_TIMED(ctx, s, "k_apply_T_scatter<G=8>", k_apply_T_scatter<T, 8><<<blocks, kApThreads, 0, s>>>(n, rp, col, c, g, o));
+    }
+    return MAFP_OK;
+  }
   if (G == 4) {
     MAFP_TIMED(ctx, s, "k_apply_T<G=4>", k_apply_T<T, 4><<<blocks, kApThreads, 0, s>>>(n, rp, col, tloc, c, g, o));
   } else if (G == 16) {
@@ -158,6 +227,7 @@ static void launch_apply_T(mafp_ctx *ctx, cudaStream_t s, int64_t n, const long 
   } else {
     MAFP_TIMED(ctx, s, "k_apply_T<G=8>", k_apply_T<T, 8><<<blocks, kApThreads, 0, s>>>(n, rp, col, tloc, c, g, o));
   }
+  return MAFP_OK;
 }
 
 int apply_ops(mafp_ctx *ctx, int64_t n, int32_t dtype, const int64_t *row_ptr, const int32_t *col,
@@ -173,8 +243,10 @@ int apply_ops_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const int64_t *r
                        const int32_t *col, const uint16_t *tloc, const void *coef,
                        const void *gout, void *gfields, cudaStream_t s) {
   const long long *rp = reinterpret_cast<const long long *>(row_ptr);
-  if (dtype == MAFP_F64) launch_apply_T<double>(ctx, s, n, rp, col, tloc, coef, gout, gfields);
-  else launch_apply_T<float>(ctx, s, n, rp, col, tloc, coef, gout, gfields);
+  const int rc = dtype == MAFP_F64
+                     ? launch_apply_T<double>(ctx, s, n, rp, col, tloc, coef, gout, gfields)
+                     : launch_apply_T<float>(ctx, s, n, rp, col, tloc, coef, gout, gfields);
+  if (rc) return rc;
   MAFP_LAUNCH_CHECK(ctx);
   return MAFP_OK;
 }

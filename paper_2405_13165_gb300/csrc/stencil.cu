@@ -14,7 +14,7 @@ namespace mafp {
 
 __global__ void k_reset_queue(DevStatus *st) { st->fallback_count = 0; }
 
-constexpr int kGatherU = 4;   // neighbours a lane gathers ahead of use
+constexpr int kGatherU = 2;   // neighbours a lane gathers ahead of use
 constexpr int kGatherR = 2;   // the same in the refinement pass (more live registers)
 
 // Process particle i with a group of G lanes.  Returns (through *result)

@@ -319,11 +319,12 @@ def transpose_map(ctx: Context, row_ptr, col, tloc, stream=None):
 
 def apply_ops_backward(ctx: Context, row_ptr, col, tloc, coef, gout, gfields, dtype=F32_REFINED,
                        stream=None):
+    """Adjoint of apply_ops w.r.t. the fields; tloc None scatters with atomics."""
     n = row_ptr.numel() - 1
     rd = real_dtype(dtype)
     _need(row_ptr, "row_ptr", torch.int64)
     _need(col, "col", torch.int32)
-    _need(tloc, "tloc", None, col.numel())
+    _need(tloc, "tloc", None, col.numel(), allow_none=True)
     _need(coef, "coef", rd, 4 * col.numel())
     _need(gout, "gout", rd, 16 * n)
     _need(gfields, "gfields", rd, 4 * n)

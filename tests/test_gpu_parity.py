@@ -177,21 +177,25 @@ def test_film_to_bulk_detection(orc, dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-def test_apply_transpose(orc, dtype):
+@pytest.mark.parametrize("scatter", [False, True])
+def test_apply_transpose(orc, dtype, scatter):
     # adjoint identity <apply(f), g> = <f, apply_T(g)> on the GPU's own
-    # stencils, and apply_T against the oracle's transpose of its own stencils
+    # stencils, and apply_T against the oracle's transpose of its own stencils;
+    # gathered through the transpose map, or scattered with atomics (no map)
     c = C.config_small()
     o = _oracle_all(orc, c)
     g, pipe, d, ctx = run_gpu(c, dtype)
     n = c.n
     rp, col = pipe.csr(n)
-    tloc = torch.empty(col.numel(), dtype=torch.int16, device="cuda")
-    M.transpose_map(ctx, rp, col, tloc)
+    tloc = None
+    if not scatter:
+        tloc = torch.empty(col.numel(), dtype=torch.int16, device="cuda")
+        M.transpose_map(ctx, rp, col, tloc)
     rng = np.random.default_rng(3)
     G = rng.normal(size=(n, 4, 4))
     rd = M.real_dtype(dtype)
     gt = torch.tensor(G, dtype=rd, device="cuda")
-    gf = torch.zeros((n, 4), dtype=rd, device="cuda")
+    gf = torch.full((n, 4), 7.0, dtype=rd, device="cuda")   # overwritten by both forms
     M.apply_ops_backward(ctx, rp, col, tloc, pipe.coef, gt, gf, dtype)
     torch.cuda.synchronize()
     got = gf.double().cpu().numpy()
