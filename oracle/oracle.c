@@ -669,8 +669,14 @@ void orc_stencil_grad(int64_t n, const double *P, const uint8_t *model, const in
                       const int32_t *col, const orc_params *prm, const double *fields,
                       const double *gout, double *gpos) {
   for (int64_t k = 0; k < 4 * n; ++k) gpos[k] = 0.0;
-  for (int64_t i = 0; i < n; ++i)
+  for (int64_t i = 0; i < n; ++i) {
+    /* a row whose 16 output gradients are all zero contributes exactly zero
+       (every term of its adjoint is a product with gbar = 0): skip it */
+    int live = 0;
+    for (int k = 0; k < 16; ++k) live |= gout[16 * i + k] != 0.0;
+    if (!live) continue;
     stencil_grad_one(i, P, model, row_ptr, col, prm, fields, gout, gpos);
+  }
 }
 
 /* Eq. GFDM_Definition: d*_i u = sum_{j in S_i} c*_ij u_j, for the four fields. */

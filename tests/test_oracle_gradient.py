@@ -85,3 +85,24 @@ def test_gradient_zero_for_deficient_rows(orc):
     g = orc.stencil_grad(P, np.zeros(4, np.uint8), rp, col, np.ones((4, 4)),
                          np.ones((4, 4, 4)))
     assert np.all(g == 0)
+
+
+def test_gradient_is_additive_over_rows(orc):
+    # the gradient is linear in dL/dout, so splitting the rows into two sets and
+    # adding the two gradients gives the full one (also covers rows whose output
+    # gradient is zero, which contribute nothing)
+    c = C.cube_on_sheet(0.05, cube=0.4, sheet=1.0)
+    P = c.pos_h.astype(np.float64)
+    F = c.vp.astype(np.float64)
+    rp, col = orc.neighbours(P)
+    rng = np.random.default_rng(7)
+    G = rng.normal(size=(c.n, 4, 4))
+    part = rng.uniform(size=c.n) < 0.3
+    Ga, Gb = G.copy(), G.copy()
+    Ga[~part] = 0.0
+    Gb[part] = 0.0
+    g = orc.stencil_grad(P, c.model, rp, col, F, G)
+    ga = orc.stencil_grad(P, c.model, rp, col, F, Ga)
+    gb = orc.stencil_grad(P, c.model, rp, col, F, Gb)
+    assert np.all(np.abs(ga + gb - g) <= 1e-12 * np.abs(g).max())
+    assert np.any(ga[:, :3] != 0) and np.any(gb[:, :3] != 0)
