@@ -63,7 +63,7 @@ typedef struct {
   double alpha_film;     /* alpha of Eq. Height (not given in the paper; default 4) */
   double alpha_w;        /* shape of the GFDM weight W(s) (not given; default 4) */
   double c_psi;          /* (r_min + r_max)/2 of Sec. 5.2 (not given; default 1/3.5) */
-  double cond_fp64;      /* FP32 stencils whose condition estimate exceeds this are redone in FP64 */
+  double cond_fp64;      /* FP32 stencils whose condition estimate exceeds this are redone in FP64 (1e4) */
   double eps_band;       /* FP32 eps_lambda within this of its threshold -> FP64 retake */
   double angle_band;     /* FP32 |n.w3| within this of cos(theta*) -> FP64 retake */
   double hfilm_band;     /* FP32 H_film within this relative band of h3D -> FP64 retake */

@@ -401,6 +401,171 @@ def config_batched(nclouds: int = 256, **kw) -> tuple[Cloud, np.ndarray]:
     return concat(parts, f"batched({len(parts)} clouds)"), off
 
 
+# ---------------------------------------------------------------- tray loop
+TRAY_SHEET = (2.0, 1.0)          # film sheet extent (m)
+TRAY_JET_FOOT = (0.45, 0.5)      # where the jet axis meets the plate
+TRAY_JET_TILT = math.radians(30.0)
+TRAY_JET_R, TRAY_JET_LEN = 0.02, 0.3
+TRAY_BLOBS = 256
+
+
+def _tray_heights(dx: float, rng: np.random.Generator) -> np.ndarray:
+    """Puddle depth in layers per film site: the largest of TRAY_BLOBS Gaussian
+    bumps (amplitude U[2, 8] dx, sigma U[10, 40] dx, cut at 3 sigma), rounded
+    to whole layers; blobs keep clear of the jet foot."""
+    ni, nj = int(round(TRAY_SHEET[0] / dx)), int(round(TRAY_SHEET[1] / dx))
+    H = np.zeros((ni, nj), np.float32)
+    placed = 0
+    while placed < TRAY_BLOBS:
+        cx = rng.uniform(0.1, TRAY_SHEET[0] - 0.1)
+        cy = rng.uniform(0.1, TRAY_SHEET[1] - 0.1)
+        sig = rng.uniform(10.0, 40.0) * dx
+        amp = rng.uniform(2.0, 8.0)
+        if math.hypot(cx - TRAY_JET_FOOT[0], cy - TRAY_JET_FOOT[1]) < 3.0 * sig + 0.2:
+            continue
+        placed += 1
+        i0, i1 = max(0, int((cx - 3 * sig) / dx)), min(ni, int((cx + 3 * sig) / dx) + 1)
+        j0, j1 = max(0, int((cy - 3 * sig) / dx)), min(nj, int((cy + 3 * sig) / dx) + 1)
+        xs = (np.arange(i0, i1) + 0.5) * dx - cx
+        ys = (np.arange(j0, j1) + 0.5) * dx - cy
+        r2 = xs[:, None] ** 2 + ys[None, :] ** 2
+        bump = amp * np.exp(-r2 / (2.0 * sig * sig))
+        bump[r2 > 9.0 * sig * sig] = 0.0
+        np.maximum(H[i0:i1, j0:j1], bump.astype(np.float32), out=H[i0:i1, j0:j1])
+    return np.floor(H + 0.5).astype(np.int32)
+
+
+def _tray_jet(dx: float):
+    """Lattice sites (i, j, k) of the inclined jet column (axis tilted from the
+    vertical towards +x, ending on the plate) and their free-surface flags."""
+    a = np.array([math.sin(TRAY_JET_TILT), 0.0, math.cos(TRAY_JET_TILT)])
+    fx, fy = TRAY_JET_FOOT
+    r, L = TRAY_JET_R, TRAY_JET_LEN
+    i0 = int((fx - r) / dx) - 1
+    i1 = int((fx + L * a[0] + r) / dx) + 2
+    j0, j1 = int((fy - r) / dx) - 1, int((fy + r) / dx) + 2
+    nk = int((L * a[2] + r) / dx) + 2
+    X = (np.arange(i0, i1) + 0.5) * dx - fx
+    Y = (np.arange(j0, j1) + 0.5) * dx - fy
+    I, J = np.meshgrid(X, Y, indexing="ij")
+    occ = np.zeros((I.shape[0], I.shape[1], nk), bool)
+    for k in range(nk):                     # one layer at a time (bounded memory)
+        Z = k * dx
+        s = I * a[0] + J * a[1] + Z * a[2]
+        rad2 = (I - s * a[0]) ** 2 + (J - s * a[1]) ** 2 + (Z - s * a[2]) ** 2
+        occ[:, :, k] = (rad2 <= r * r) & (s <= L)
+    pad = np.zeros((occ.shape[0] + 2, occ.shape[1] + 2, occ.shape[2] + 2), bool)
+    pad[1:-1, 1:-1, 1:-1] = occ
+    pad[1:-1, 1:-1, 0] = True                     # the plate below layer 0
+    exposed = np.zeros_like(occ)
+    for d in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+        exposed |= ~pad[1 + d[0]:pad.shape[0] - 1 + d[0], 1 + d[1]:pad.shape[1] - 1 + d[1],
+                        1 + d[2]:pad.shape[2] - 1 + d[2]]
+    oi, oj, ok = np.nonzero(occ)
+    return oi + i0, oj + j0, ok, exposed[oi, oj, ok]
+
+
+def tray_count(dx: float, seed: int = SEED_BASE + 5) -> int:
+    rng = np.random.default_rng(seed)
+    L = _tray_heights(dx, rng)
+    ji, jj, jk, _ = _tray_jet(dx)
+    foot = np.zeros_like(L, bool)
+    ok = (jk == 0) & (ji >= 0) & (ji < L.shape[0]) & (jj >= 0) & (jj < L.shape[1])
+    foot[ji[ok], jj[ok]] = True
+    return int(L.sum() + ji.size + ((L == 0) & ~foot).sum())
+
+
+def tray_cloud(dx: float, film_h_factor: float = 0.3, seed: int = SEED_BASE + 5) -> Cloud:
+    """Tray-cleaning shape: a 2 x 1 m film sheet with pooled 3D puddles (columns
+    under Gaussian bumps up to 8 layers) and an inclined 3D jet column
+    (r = 0.02 m, 0.3 m long, 30 degrees from the vertical) standing on it.
+    3D particles in layer 0 are WALL, those with an empty lattice neighbour (or
+    the top of a column) FREE_SURFACE, the rest INTERIOR; film sites under 3D
+    matter are removed."""
+    rng = np.random.default_rng(seed)
+    L = _tray_heights(dx, rng)
+    ni, nj = L.shape
+    # puddle columns
+    ci, cj = np.nonzero(L > 0)
+    Lc = L[ci, cj]
+    rep = np.repeat(np.arange(ci.size), Lc)
+    pk = np.arange(rep.size) - np.repeat(np.cumsum(Lc) - Lc, Lc)
+    pi, pj = ci[rep], cj[rep]
+    Lp = np.pad(L, 1)
+    side = np.minimum.reduce([Lp[pi, pj + 1], Lp[pi + 2, pj + 1], Lp[pi + 1, pj], Lp[pi + 1, pj + 2]])
+    ptype = np.where(pk == 0, TYPE_WALL,
+                     np.where((pk == L[pi, pj] - 1) | (side <= pk), TYPE_FREE_SURFACE,
+                              TYPE_INTERIOR)).astype(np.uint8)
+    # jet column
+    ji, jj, jk, jexp = _tray_jet(dx)
+    jtype = np.where(jk == 0, TYPE_WALL,
+                     np.where(jexp, TYPE_FREE_SURFACE, TYPE_INTERIOR)).astype(np.uint8)
+    foot = np.zeros_like(L, bool)
+    ok = (jk == 0) & (ji >= 0) & (ji < ni) & (jj >= 0) & (jj < nj)
+    foot[ji[ok], jj[ok]] = True
+    fi, fj = np.nonzero((L == 0) & ~foot)
+    xyz = np.concatenate([
+        np.stack([(pi + 0.5) * dx, (pj + 0.5) * dx, pk * dx], 1),
+        np.stack([(ji + 0.5) * dx, (jj + 0.5) * dx, jk * dx], 1),
+        np.stack([(fi + 0.5) * dx, (fj + 0.5) * dx, np.zeros(fi.size)], 1)])
+    model = np.concatenate([np.full(pi.size, MODEL_3D), np.full(ji.size, MODEL_3D),
+                            np.full(fi.size, MODEL_2D)]).astype(np.uint8)
+    ptype = np.concatenate([ptype, jtype, np.full(fi.size, TYPE_WALL, np.uint8)])
+    planar = ptype == TYPE_WALL
+    normal = np.zeros((xyz.shape[0], 4), np.float32)
+    normal[planar, 2] = 1.0
+    xyz = _jitter(xyz, planar, dx, rng)
+    return _finish(xyz, model, ptype, normal, film_h_factor * dx, dx, rng,
+                   f"tray(dx={dx:.6g})")
+
+
+def config_tray(n_target: int = 16_000_000, seed: int = SEED_BASE + 5) -> Cloud:
+    """Tray shape with dx bisected to n_target particles (within 1 %), in cell order."""
+    lo, hi = 2e-4, 0.01
+    for _ in range(60):
+        mid = math.sqrt(lo * hi)
+        cnt = tray_count(mid, seed)
+        if abs(cnt - n_target) <= 0.01 * n_target:
+            break
+        if cnt > n_target:
+            lo = mid
+        else:
+            hi = mid
+    return cell_sorted(tray_cloud(mid, seed=seed))
+
+
+def tray_velocity(dx: float, seed: int = SEED_BASE + 5 * 1000) -> dict:
+    """Smooth random displacement field of the tray loop (float32 parameters):
+    d(x) = sum_m a_m e_m b(u_m),  u_m = frac((kappa_m . x + phi_m) / (2 pi)),
+    b(u) = 16 u^2 (1 - u)^2 - 16/30 (a C2-periodic, zero-mean bump), four
+    modes with e_m and kappa_m uniform on the sphere, |kappa_m| ~ U[2, 10]
+    rad/m, amplitudes scaled so that |d| <= 0.2 dx per step.  Built from +, *
+    and floor only, so float32 evaluations agree bit for bit on any IEEE
+    device when the operations are taken in the stated order."""
+    rng = np.random.default_rng(seed)
+    e = rng.normal(size=(4, 3))
+    e /= np.linalg.norm(e, axis=1, keepdims=True)
+    k = rng.normal(size=(4, 3))
+    k /= np.linalg.norm(k, axis=1, keepdims=True)
+    k *= rng.uniform(2.0, 10.0, size=(4, 1))
+    phi = rng.uniform(0.0, 2.0 * math.pi, size=4)
+    a = rng.uniform(0.5, 1.0, size=4)
+    a *= 0.2 * dx / (a.sum() * (16.0 / 30.0))     # |b| <= 16/30
+    f32 = np.float32
+    return {"e": e.astype(f32), "kappa": k.astype(f32), "phi": phi.astype(f32),
+            "amp": a.astype(f32), "inv_2pi": f32(1.0 / (2.0 * math.pi)),
+            "mean": f32(16.0 / 30.0), "zmin": f32(0.5 * dx)}
+
+
+def tray_sphere(step: int) -> tuple[np.ndarray, float, float]:
+    """User criterion of the tray loop (a sphere on the plate sweeping along x,
+    like the distance criterion of Sec. 7.4): (centre, radius, trailing shell).
+    Film particles inside the sphere are asked to become 3D; 3D particles in
+    the shell it has just left are asked to become 2D."""
+    c = np.array([0.15 + 0.09 * step, 0.5, 0.0])
+    return c, 0.2, 0.09
+
+
 def cell_sorted(cloud: Cloud, cell_factor: float = 1.0 + 1e-6) -> Cloud:
     """Permute a cloud into cell order: cells of edge max(h) * cell_factor from
     the bounding-box minimum, keys (cz * ny + cy) * nx + cx, stable in index.

@@ -94,7 +94,7 @@ void mafp_default_params(mafp_params *p) {
   p->alpha_film = 4.0;
   p->alpha_w = 4.0;
   p->c_psi = 1.0 / 3.5;
-  p->cond_fp64 = 1e5;
+  p->cond_fp64 = 1e4;
   p->eps_band = 1e-4;
   p->angle_band = 1e-3;
   p->hfilm_band = 1e-4;

@@ -20,6 +20,8 @@ OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENOTIMPL, ENONFINITE = 0, -1, -2, -3, -4
 MAX_CLOUDS = 65536          # largest batch of mafp_build_neighbours_batched
 F32_REFINED, F32_PLAIN, F64 = 0, 1, 2
 MODEL_3D, MODEL_2D = 0, 1
+TYPE_INTERIOR, TYPE_FREE_SURFACE, TYPE_WALL = 0, 1, 2
+USER_TO_2D, USER_TO_3D = 1, 2
 STENCIL_OK, STENCIL_DEFICIENT, STENCIL_FP64 = 0, 1, 2
 _CODES = {0: "OK", -1: "EINVAL", -2: "ECAPACITY", -3: "ECUDA", -4: "ETIMEOUT", -5: "ENOTIMPL",
           -6: "ENONFINITE"}

@@ -82,3 +82,37 @@ def column_error(a, b):
     normwise = diff.max(0) / np.where(scale > 0, scale, 1)
     comp = diff / np.maximum(np.abs(b).reshape(-1, 16), 1e-3 * scale)
     return normwise, np.percentile(comp, 99, axis=0) if comp.size else np.zeros(16)
+
+
+def storage_bound(rp, col, coef, fields, rows=None):
+    """Per output element, 2^-24 sum_j |c_ij^op| |u_j - u_i| (FP64 coefficients):
+    what a relative coefficient error of one FP32 unit roundoff can do to that
+    output.  Near-degenerate rows (thin 3D layers, condition 1e3 and up) have
+    large, cancelling coefficients; there an output is this many times more
+    sensitive than its own size suggests."""
+    n = len(rp) - 1
+    F = np.asarray(fields, np.float64)
+    rows_of = np.repeat(np.arange(n), np.diff(rp))
+    keep = np.ones(rows_of.size, bool) if rows is None else np.isin(rows_of, rows)
+    r, j, c = rows_of[keep], col[keep], np.abs(coef[keep])
+    du = np.abs(F[j] - F[r])
+    b = np.zeros((n, 4, 4))
+    for f in range(4):
+        for op in range(4):
+            b[:, f, op] = np.bincount(r, c[:, op] * du[:, f], minlength=n)
+    return b * 2.0 ** -24
+
+
+# Refined FP32 stencils agree with FP64 to ~1e-6 of a row's largest coefficient
+# (about 16 unit roundoffs: measured 1e-6 .. 3.5e-6 up to condition 1e5); an
+# output inherits that times its sensitivity.  32 roundoffs leaves 2x margin.
+COEF_ROUNDOFFS = 32.0
+
+
+def outputs_within(a, b, bound, tol):
+    """|a - b| <= tol * (column max of |b|) + COEF_ROUNDOFFS * bound, elementwise;
+    returns the worst ratio of the error to that allowance (<= 1 passes)."""
+    scale = np.abs(b).reshape(-1, 16).max(0)
+    allow = tol * scale + COEF_ROUNDOFFS * bound.reshape(-1, 16)
+    err = np.abs(a - b).reshape(-1, 16)
+    return float((err / np.where(allow > 0, allow, 1e-300)).max()) if err.size else 0.0
