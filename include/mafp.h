@@ -139,6 +139,16 @@ int mafp_build_neighbours(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *p
                           int64_t *row_ptr, int32_t *col, int64_t cap_nnz, int64_t *nnz_dev,
                           int32_t *order, void *stream);
 
+/* mafp_cell_order -- the first stage of mafp_build_neighbours alone (grid of
+ * edge >= max h over the bounding box, cell keys, stable radix sort): writes
+ * the permutation that puts the particles in cell order, order[s] = index of
+ * the particle at sorted position s, without building neighbour lists.  A
+ * time loop re-sorts its particles by it so the next neighbour build takes
+ * the in-order path.  order int32 [n] written; the status block reports
+ * cells_identity as mafp_build_neighbours does. */
+int mafp_cell_order(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h, int32_t *order,
+                    void *stream);
+
 /* Largest nclouds of mafp_build_neighbours_batched. */
 #define MAFP_MAX_CLOUDS 65536
 

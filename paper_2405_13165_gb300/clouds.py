@@ -566,15 +566,16 @@ def tray_sphere(step: int) -> tuple[np.ndarray, float, float]:
     return c, 0.2, 0.09
 
 
-def cell_sorted(cloud: Cloud, cell_factor: float = 1.0 + 1e-6) -> Cloud:
-    """Permute a cloud into cell order: cells of edge max(h) * cell_factor from
-    the bounding-box minimum, keys (cz * ny + cy) * nx + cx, stable in index.
+def cell_order(pos_h: np.ndarray, cell_factor: float = 1.0 + 1e-6) -> np.ndarray:
+    """Cell order of a cloud: cells of edge max(h) * cell_factor from the
+    bounding-box minimum, keys (cz * ny + cy) * nx + cx, stable in index;
+    returns the permutation (sorted position -> index).
 
     A Lagrangian code keeps its particles in this order between steps; it is
     the order the neighbour search's own cell sort produces, so a cloud in it
     takes the search's sorted path.  Input layout only (no method arithmetic).
     """
-    P = cloud.pos_h.astype(np.float64)
+    P = pos_h.astype(np.float64)
     lo = P[:, :3].min(0)
     hi = P[:, :3].max(0)
     c = float(P[:, 3].max()) * cell_factor
@@ -583,4 +584,9 @@ def cell_sorted(cloud: Cloud, cell_factor: float = 1.0 + 1e-6) -> Cloud:
     cc = np.floor((P[:, :3] - lo) * inv_c)
     cc = np.clip(cc, 0, dim - 1).astype(np.int64)
     key = (cc[:, 2] * int(dim[1]) + cc[:, 1]) * int(dim[0]) + cc[:, 0]
-    return cloud.take(np.argsort(key, kind="stable"))
+    return np.argsort(key, kind="stable")
+
+
+def cell_sorted(cloud: Cloud, cell_factor: float = 1.0 + 1e-6) -> Cloud:
+    """The cloud permuted into cell order (see cell_order)."""
+    return cloud.take(cell_order(cloud.pos_h, cell_factor))

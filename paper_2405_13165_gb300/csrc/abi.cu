@@ -13,6 +13,7 @@ int build_neighbours(mafp_ctx *, int64_t, int32_t, const void *, int64_t *, int3
                      int64_t *, int32_t *, cudaStream_t);
 int build_neighbours_batched(mafp_ctx *, int64_t, int32_t, int32_t, const int64_t *, const void *,
                              int64_t *, int32_t *, int64_t, int64_t *, int32_t *, cudaStream_t);
+int cell_order(mafp_ctx *, int64_t, int32_t, const void *, int32_t *, cudaStream_t);
 int transpose_map(mafp_ctx *, int64_t, const int64_t *, const int32_t *, uint16_t *,
                   cudaStream_t);
 int classify_pca(mafp_ctx *, int64_t, int32_t, const void *, const uint8_t *, const uint8_t *,
@@ -254,6 +255,18 @@ int mafp_build_neighbours(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *p
   REQUIRE(pos_h);
   REQUIRE(col);
   return build_neighbours(ctx, n, dtype, pos_h, row_ptr, col, cap_nnz, nnz_dev, order, s);
+}
+
+int mafp_cell_order(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h, int32_t *order,
+                    void *stream) {
+  if (!ctx) return MAFP_EINVAL;
+  int rc;
+  if ((rc = check_dtype(ctx, dtype)) || (rc = check_n(ctx, n))) return rc;
+  if (n == 0) return MAFP_OK;
+  REQUIRE(pos_h);
+  REQUIRE(order);
+  if (ensure_device(ctx)) return MAFP_ECUDA;
+  return cell_order(ctx, n, dtype, pos_h, order, (cudaStream_t)stream);
 }
 
 int mafp_build_neighbours_batched(mafp_ctx *ctx, int64_t n, int32_t dtype, int32_t nclouds,

@@ -740,10 +740,13 @@ __global__ void k_tmap(const long long *row_ptr, const int32_t *col, int64_t n, 
 }
 
 // ------------------------------------------------------------------ host side
+// A1: grids, cell keys, stable radix sort, cell ranges, sorted positions and
+// (optionally) the cell order.  On return the sorted keys / indices are in
+// *kin / *vin.
 template <typename T>
-static int build_neighbours_t(mafp_ctx *ctx, int64_t n, int nb, const long long *cloud_off,
-                              const void *pos_h, int64_t *row_ptr, int32_t *col,
-                              int64_t cap_nnz, int64_t *nnz_dev, int32_t *order, cudaStream_t s) {
+static int sort_into_cells_t(mafp_ctx *ctx, int64_t n, int nb, const long long *cloud_off,
+                             const void *pos_h, int32_t *order, uint32_t **kin_out,
+                             int32_t **vin_out, cudaStream_t s) {
   using V = vec4_t<T>;
   const V *pos = reinterpret_cast<const V *>(pos_h);
   const int sms = sm_count();
@@ -793,6 +796,23 @@ static int build_neighbours_t(mafp_ctx *ctx, int64_t n, int nb, const long long 
   MAFP_TIMED(ctx, s, "k_identity_flag",
              k_identity_flag<<<1, 1, 0, s>>>(ctx->d_status));
   MAFP_LAUNCH_CHECK(ctx);
+  *kin_out = kin;
+  *vin_out = vin;
+  return MAFP_OK;
+}
+
+template <typename T>
+static int build_neighbours_t(mafp_ctx *ctx, int64_t n, int nb, const long long *cloud_off,
+                              const void *pos_h, int64_t *row_ptr, int32_t *col,
+                              int64_t cap_nnz, int64_t *nnz_dev, int32_t *order, cudaStream_t s) {
+  using V = vec4_t<T>;
+  const int sms = sm_count();
+  uint32_t *kin = nullptr;
+  int32_t *vin = nullptr;
+  int rc0 = sort_into_cells_t<T>(ctx, n, nb, cloud_off, pos_h, order, &kin, &vin, s);
+  if (rc0) return rc0;
+  V *spos = reinterpret_cast<V *>(ctx->spos);
+  CloudGrids cg{ctx->d_grids, ctx->cell_base, nb, ctx->d_grid};
   const int nbr_blocks = sms * 8;
   int32_t *n_overflow = ctx->n_ucell + 1;
   const int64_t stride = ctx->cap_particles;
@@ -836,6 +856,16 @@ int build_neighbours(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h,
                                       nnz_dev, order, s);
   return build_neighbours_t<float>(ctx, n, 1, ctx->one_cloud, pos_h, row_ptr, col, cap_nnz,
                                    nnz_dev, order, s);
+}
+
+int cell_order(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h, int32_t *order,
+               cudaStream_t s) {
+  MAFP_TIMED(ctx, s, "k_set_one_cloud", k_set_one_cloud<<<1, 1, 0, s>>>(ctx->one_cloud, n));
+  uint32_t *kin = nullptr;
+  int32_t *vin = nullptr;
+  if (dtype == MAFP_F64)
+    return sort_into_cells_t<double>(ctx, n, 1, ctx->one_cloud, pos_h, order, &kin, &vin, s);
+  return sort_into_cells_t<float>(ctx, n, 1, ctx->one_cloud, pos_h, order, &kin, &vin, s);
 }
 
 int build_neighbours_batched(mafp_ctx *ctx, int64_t n, int32_t dtype, int32_t nclouds,

@@ -86,6 +86,7 @@ def lib():
         L.mafp_reset_status.argtypes = [p, p]
         L.mafp_build_neighbours.argtypes = [p, i64, i32, p, p, p, i64, p, p, p]
         L.mafp_build_neighbours_batched.argtypes = [p, i64, i32, i32, p, p, p, p, i64, p, p, p]
+        L.mafp_cell_order.argtypes = [p, i64, i32, p, p, p]
         L.mafp_classify_pca.argtypes = [p, i64, i32] + [p] * 17
         L.mafp_build_stencils.argtypes = [p, i64, i32, p, p, p, p, p, p, p, p, p]
         L.mafp_apply_ops.argtypes = [p, i64, i32, p, p, p, p, p, p]
@@ -98,7 +99,7 @@ def lib():
         L.mafp_profile.argtypes = [p, i32]
         L.mafp_profile_read.argtypes = [p, p, i32, p]
         for name in ("mafp_set_tuning", "mafp_get_tuning", "mafp_profile", "mafp_profile_read", "mafp_create", "mafp_destroy", "mafp_get_status", "mafp_reset_status",
-                     "mafp_build_neighbours", "mafp_build_neighbours_batched",
+                     "mafp_build_neighbours", "mafp_build_neighbours_batched", "mafp_cell_order",
                      "mafp_classify_pca", "mafp_build_stencils",
                      "mafp_apply_ops", "mafp_transpose_map", "mafp_apply_ops_backward",
                      "mafp_build_stencils_backward", "mafp_remap_switched"):
@@ -219,6 +220,15 @@ def build_neighbours(ctx: Context, pos_h, row_ptr, col, nnz=None, order=None, dt
     ctx.check(lib().mafp_build_neighbours(ctx.handle, n, dtype, _ptr(pos_h), _ptr(row_ptr),
                                           _ptr(col), col.numel(), _ptr(nnz), _ptr(order),
                                           _stream(stream)))
+
+
+def cell_order(ctx: Context, pos_h, order, dtype=F32_REFINED, stream=None):
+    """Permutation into cell order (order[s] = particle at sorted position s)."""
+    n = pos_h.shape[0]
+    _need(pos_h, "pos_h", real_dtype(dtype), 4 * n)
+    _need(order, "order", torch.int32, n)
+    ctx.check(lib().mafp_cell_order(ctx.handle, n, dtype, _ptr(pos_h), _ptr(order),
+                                    _stream(stream)))
 
 
 def build_neighbours_batched(ctx: Context, cloud_offset, pos_h, row_ptr, col, nnz=None, order=None,

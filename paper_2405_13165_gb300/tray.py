@@ -7,6 +7,7 @@ the data mapping of Sec. 5), then moves the particles.
              stencils -> apply                     (derivatives for the solver)
              remap_switched                        (particle count changes here)
              advect by the smooth displacement field of clouds.tray_velocity
+             re-sort into cell order (mafp_cell_order)
 
 The library calls do the path; this module only marshals buffers and applies
 the workload's own rules (user criterion, advection) with elementwise torch
@@ -102,6 +103,7 @@ class TrayLoop:
         self.user = torch.zeros(cap, dtype=torch.uint8, device=device)
         self.old2new = torch.zeros(cap, dtype=torch.int32, device=device)
         self.n_out = torch.zeros(1, dtype=torch.int64, device=device)
+        self.order = torch.zeros(cap, dtype=torch.int32, device=device)
 
     def cloud_dict(self) -> dict:
         n, S = self.n, self.cur
@@ -127,7 +129,13 @@ class TrayLoop:
         to2d, to3d, deleted, n_new = (int(v) for v in counts)
         T = self.nxt
         advect(T["pos_h"][:n_new], T["model"][:n_new], T["type"][:n_new], self.vel)
-        self.cur, self.nxt = self.nxt, self.cur
+        # back into cell order (remap appends, advection drifts), so the next
+        # neighbour build takes the in-order path
+        order = self.order[:n_new]
+        M.cell_order(self.ctx, T["pos_h"][:n_new], order)
+        idx = order.long()
+        for key, v in T.items():
+            torch.index_select(v[:n_new], 0, idx, out=S[key][:n_new])
         self.n = n_new
         return {"step": k, "n_in": n, "n_out": n_new, "to2d": to2d, "to3d": to3d,
                 "deleted": deleted, "added": n_new - (n - deleted)}

@@ -85,6 +85,24 @@ def test_random_cloud_variable_h_unsorted(orc, seed, dtype):
                                rtol=1e-5 if dtype != M.F64 else 1e-12)
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_cell_order_matches_grid_convention(dtype):
+    # the permutation of the first neighbour stage alone, against the cell
+    # ordering the input generator uses (same grid, keys, stable sort)
+    c = C.random_cloud(20000, seed=9, h_lo=0.05, h_hi=0.08)
+    ctx = M.Context(c.n)
+    rd = M.real_dtype(dtype)
+    order = torch.empty(c.n, dtype=torch.int32, device="cuda")
+    M.cell_order(ctx, torch.tensor(c.pos_h, dtype=rd, device="cuda"), order, dtype)
+    np.testing.assert_array_equal(order.cpu().numpy(), C.cell_order(c.pos_h))
+    assert ctx.status()["cells_identity"] == 0
+    s = C.cell_sorted(c)
+    M.cell_order(ctx, torch.tensor(s.pos_h, dtype=rd, device="cuda"), order, dtype)
+    np.testing.assert_array_equal(order.cpu().numpy(), np.arange(c.n))
+    assert ctx.status()["cells_identity"] == 1
+    ctx.close()
+
+
 def test_neighbours_past_one_scan_chunk(orc):
     # 4.6M rows: more than 1024 scan tiles of 4096 rows, so the tile-sum scan
     # takes several chunks and every warp of its block holds live tiles

@@ -68,7 +68,8 @@ def initial_state(cloud) -> dict:
 
 
 def step(state: dict, k: int, vel: dict, rows=None) -> tuple[dict, dict]:
-    """One loop step; returns (next state, what the step computed)."""
+    """One loop step (ending with the re-sort into cell order); returns (next
+    state, what the step computed)."""
     P = state["pos_h"]
     model = state["model"]
     rp, col = O.neighbours(P)
@@ -82,6 +83,8 @@ def step(state: dict, k: int, vel: dict, rows=None) -> tuple[dict, dict]:
     nxt = {k: (np.array(v, dtype=F32) if k in KEYS_F else np.array(v, dtype=np.uint8))
            for k, v in nxt.items()}
     advect(nxt, vel)
+    order = C.cell_order(nxt["pos_h"])
+    nxt = {k: np.ascontiguousarray(v[order]) for k, v in nxt.items()}
     info = dict(row_ptr=rp, col=col, coef=coef, status=status, out=out, flag=flag,
                 near=cl["near"], preflag=cl["preflag"], old2new=old2new, n_out=n_out,
                 user=user)
