@@ -308,12 +308,14 @@ int build_stencils(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h,
                : dispatch_stencils<float, float, true, true>(ctx, s, n, pos_h, model, frame, rp,
                                                             col, coef, status, cond, sp);
   if (rc) return rc;
-  MAFP_TIMED(ctx, s, "k_stencil_redo<10,32>",
-             k_stencil_redo<10, 32><<<sms * 4, kStThreads, 0, s>>>(
+  // FP64 redo: small groups keep the per-particle factorisation, repeated in
+  // every lane of a group, from dominating the slow FP64 pipe
+  MAFP_TIMED(ctx, s, "k_stencil_redo<10,4>",
+             k_stencil_redo<10, 4><<<sms * 32, kStThreads, 0, s>>>(
       (const float4 *)pos_h, model, (const float4 *)frame, rp, col, (float4 *)coef, status, cond,
       sp64, ctx->d_status, ctx->fallback));
-  MAFP_TIMED(ctx, s, "k_stencil_redo<6,8>",
-             k_stencil_redo<6, 8><<<sms * 4, kStThreads, 0, s>>>(
+  MAFP_TIMED(ctx, s, "k_stencil_redo<6,4>",
+             k_stencil_redo<6, 4><<<sms * 32, kStThreads, 0, s>>>(
       (const float4 *)pos_h, model, (const float4 *)frame, rp, col, (float4 *)coef, status, cond,
       sp64, ctx->d_status, ctx->fallback));
   MAFP_LAUNCH_CHECK(ctx);

@@ -339,7 +339,7 @@ int build_stencils_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const void 
   const StParams<double> sp64 = make_params<double>(ctx->prm, 1e-12);
   const int sms = sm_count();
   MAFP_TIMED(ctx, s, "k_stencil_grad_redo<10>",
-             (k_stencil_grad_redo<10, 32><<<sms * 4, kStThreads, 0, s>>>(
+             (k_stencil_grad_redo<10, 8><<<sms * 16, kStThreads, 0, s>>>(
                  (const float4 *)pos_h, model, (const float4 *)frame, rp, col,
                  (const float4 *)fields, (const float4 *)gout, (float *)gpos, sp64,
                  ctx->d_status, ctx->fallback)));
