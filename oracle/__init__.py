@@ -77,6 +77,7 @@ def lib():
         L.orc_remap.argtypes = [i64, p, p, p, p, p, p, i64, p]
         L.orc_stencil_grad.argtypes = [i64, p, p, p, p, p, p, p, p]
         L.orc_remap.restype = i64
+        L.orc_ghost_sources.argtypes = [i64, p, p, p, p]
         _lib = L
     return _lib
 
@@ -309,3 +310,34 @@ def pipeline(cloud, prm=None, rows=None):
     coef, status, cond = stencils(cloud.pos_h, cloud.model, rp, col, rows=rows, prm=prm)
     out = apply(rp, col, coef, cloud.vp, rows=rows)
     return dict(row_ptr=rp, col=col, flag=flag, coef=coef, status=status, cond=cond, out=out, **cl)
+
+
+def ghost_sources(model, row_ptr, col):
+    """Alg. 5, first loop: 1 where S_i holds a particle of the other model."""
+    n = len(model)
+    src = np.zeros(n, np.uint8)
+    lib().orc_ghost_sources(n, _ptr(_u8(model)), _ptr(np.ascontiguousarray(row_ptr, np.int64)),
+                            _ptr(np.ascontiguousarray(col, np.int32)), _ptr(src))
+    return src
+
+
+def ghost_zone(state: dict, row_ptr, col, prm=None):
+    """Alg. 5 on a cloud with its neighbour lists: sources, one ghost per source
+    (same model, place and data), model transition of the ghosts (Alg. 3 for
+    the 3D ghosts, walls flagged, interior / free-surface ghosts as candidates;
+    Alg. 4 for the 2D ghosts), keeping the ghosts that transition produced.
+    Returns (union state: regular particles then ghosts, ghost sources, the
+    intermediate ghost flags, n_ghost_intermediate)."""
+    model = np.asarray(state["model"])
+    src = ghost_sources(model, row_ptr, col)
+    idx = np.nonzero(src)[0]
+    ghost = {k: np.array(v)[idx] for k, v in state.items()}
+    ghost["last"] = np.zeros(idx.size, np.uint8)
+    gm, gt = ghost["model"], ghost["ptype"]
+    gflag = np.where(gm == 1, 2, np.where(gt == 2, 1, 0)).astype(np.uint8)
+    grp, gcol = neighbours(ghost["pos_h"])
+    out, _, n_out = remap(ghost, gflag, grp, gcol, prm=prm)
+    keep = out["last"] == 1
+    union = {k: np.concatenate([np.asarray(state[k]), np.asarray(out[k])[keep].astype(
+        np.asarray(state[k]).dtype)]) for k in state}
+    return union, src, gflag, idx.size

@@ -856,3 +856,16 @@ int64_t orc_remap(int64_t n, const orc_state *in, const uint8_t *flag, const int
   free(owner);
   return n_out;
 }
+
+/* ---------------------------------------------------------------------------
+ * Buffer zone, Sec. 5.3 (Alg. 5), first loop: a particle is a ghost source
+ * when a particle of the other model lies in its neighbourhood S_i.
+ * ------------------------------------------------------------------------- */
+void orc_ghost_sources(int64_t n, const uint8_t *model, const int64_t *row_ptr,
+                       const int32_t *col, uint8_t *src) {
+  for (int64_t i = 0; i < n; ++i) {
+    src[i] = 0;
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+      if (model[col[e]] != model[i]) src[i] = 1;
+  }
+}

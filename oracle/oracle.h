@@ -106,4 +106,8 @@ int64_t orc_remap(int64_t n, const orc_state *in, const uint8_t *flag, const int
 #ifdef __cplusplus
 }
 #endif
+/* Alg. 5, first loop: src[i] = 1 when S_i holds a particle of the other model. */
+void orc_ghost_sources(int64_t n, const uint8_t *model, const int64_t *row_ptr,
+                       const int32_t *col, uint8_t *src);
+
 #endif

@@ -401,6 +401,63 @@ def config_batched(nclouds: int = 256, **kw) -> tuple[Cloud, np.ndarray]:
     return concat(parts, f"batched({len(parts)} clouds)"), off
 
 
+# ------------------------------------------------------- model interface strip
+QUAD_FIELDS = np.array([       # u, v, w, p = c0 + c1 x + c2 y + c3 x^2 + c4 x y + c5 y^2
+    [1.0, 2.0, -1.0, 0.5, 1.0, -0.3],
+    [-0.5, 0.3, 0.8, -1.2, 0.4, 0.9],
+    [0.2, -1.0, 0.5, 0.7, -0.6, 0.25],
+    [3.0, 0.1, 0.2, 0.05, 0.8, -0.4]])
+
+
+def interface_strip(dx: float = 0.02, layers: int = 3, extent=(1.0, 0.5), x_split: float = 0.5,
+                    quadratic: bool = False, columns: bool = False,
+                    seed: int = SEED_BASE + 6) -> Cloud:
+    """Film (2D) for x < x_split and a 3D layer of `layers` particles for
+    x >= x_split, side by side on the plate (the two-model arrangement of the
+    advection tests of Sec. 7.2).  The film height is (layers - 1) dx, so a
+    film particle lifted to 3D (Alg. 4, psi~ = dx) matches the layer.  3D
+    particles in layer 0 are WALL, the top layer and the columns at the strip's
+    edges FREE_SURFACE.  quadratic: fields are the depth-constant quadratics of
+    QUAD_FIELDS instead of sinusoids; columns: every 3D column shares one
+    in-plane jitter (vertical columns), otherwise the usual jitter."""
+    rng = np.random.default_rng(seed)
+    ni, nj = int(round(extent[0] / dx)), int(round(extent[1] / dx))
+    I, J = np.meshgrid(np.arange(ni), np.arange(nj), indexing="ij")
+    I, J = I.ravel(), J.ravel()
+    x = (I + 0.5) * dx
+    film = x < x_split
+    fi, fj = I[film], J[film]
+    ci, cj = I[~film], J[~film]
+    k = np.repeat(np.arange(layers)[None, :], ci.size, 0).ravel()
+    ci, cj = np.repeat(ci, layers), np.repeat(cj, layers)
+    col_id = np.repeat(np.arange(ci.size // layers), layers)
+    edge = (cj == 0) | (cj == nj - 1) | (ci == ci.min()) | (ci == ni - 1)
+    ctype = np.where(k == 0, TYPE_WALL,
+                     np.where((k == layers - 1) | edge, TYPE_FREE_SURFACE, TYPE_INTERIOR))
+    xyz = np.concatenate([np.stack([(ci + 0.5) * dx, (cj + 0.5) * dx, k * dx], 1),
+                          np.stack([(fi + 0.5) * dx, (fj + 0.5) * dx, np.zeros(fi.size)], 1)])
+    model = np.concatenate([np.full(ci.size, MODEL_3D), np.full(fi.size, MODEL_2D)]).astype(np.uint8)
+    ptype = np.concatenate([ctype, np.full(fi.size, TYPE_WALL)]).astype(np.uint8)
+    planar = ptype == TYPE_WALL
+    normal = np.zeros((xyz.shape[0], 4), np.float32)
+    normal[planar, 2] = 1.0
+    if columns:
+        # in-plane jitter shared by each 3D column (columns stay vertical)
+        cj_xy = rng.uniform(-0.1 * dx, 0.1 * dx, size=(col_id.max() + 1, 2))
+        fj_xy = rng.uniform(-0.1 * dx, 0.1 * dx, size=(fi.size, 2))
+        xyz[:, :2] += np.concatenate([cj_xy[col_id], fj_xy])
+    else:
+        xyz = _jitter(xyz, planar, dx, rng)
+    c = _finish(xyz, model, ptype, normal, (layers - 1) * dx, dx, rng,
+                f"interface_strip(dx={dx:g}, layers={layers})")
+    if quadratic:
+        X = c.pos_h[:, 0].astype(np.float64)
+        Y = c.pos_h[:, 1].astype(np.float64)
+        mono = np.stack([np.ones_like(X), X, Y, X * X, X * Y, Y * Y], 1)
+        c.vp = (mono @ QUAD_FIELDS.T).astype(np.float32)
+    return c
+
+
 # ---------------------------------------------------------------- tray loop
 TRAY_SHEET = (2.0, 1.0)          # film sheet extent (m)
 TRAY_JET_FOOT = (0.45, 0.5)      # where the jet axis meets the plate
