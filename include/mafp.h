@@ -331,6 +331,37 @@ typedef struct {
 int mafp_profile(mafp_ctx *ctx, int32_t enable);
 int mafp_profile_read(mafp_ctx *ctx, mafp_kernel_time *out, int32_t cap, int32_t *count);
 
+/* --------------------------------------------------------------------------
+ * Buffer zone of Sec. 5.3 (Alg. 5), in three calls around a transition of the
+ * ghost cloud:
+ *  mafp_ghost_sources -- first loop: src[i] = 1 when S_i (Eq. Nbd, all models;
+ *    the "within h" of Sec. 5.3 read as the neighbourhood) holds a particle of
+ *    the other model, else 0.  src uint8 [n] written.
+ *  mafp_ghost_seed -- second loop: every source is copied, in index order, as
+ *    an intermediate ghost of the same model at the same place (last = 0);
+ *    ghost_flag[g] is the transition it takes in the third loop (1: 3D wall
+ *    -> 2D, 2: 2D -> 3D, 0: interior / free-surface 3D ghost, a candidate that
+ *    Alg. 3 maps onto its nearest wall ghost); ghost_src[g] = its source
+ *    index; *n_ghost_dev = the count.  If it exceeds cap_ghost nothing is
+ *    copied and the status block records MAFP_ECAPACITY.
+ *  third loop: mafp_build_neighbours over the n_ghost intermediate ghosts,
+ *    then mafp_remap_switched with ghost_flag.
+ *  mafp_ghost_append -- the ghosts that transition produced (last == 1; a
+ *    candidate left without a wall ghost keeps its model and is dropped) are
+ *    appended behind the n_regular particles already in `all`:
+ *    *n_all_dev = n_regular + their count (MAFP_ECAPACITY above cap_all,
+ *    nothing copied).  Stencils of the regular rows built over the union then
+ *    use S_i plus the ghost neighbours of i's model (Eq. GhostDerivatives);
+ *    no derivative is taken at a ghost. */
+int mafp_ghost_sources(mafp_ctx *ctx, int64_t n, const uint8_t *model, const int64_t *row_ptr,
+                       const int32_t *col, uint8_t *src, void *stream);
+int mafp_ghost_seed(mafp_ctx *ctx, int64_t n, int32_t dtype, const mafp_state *in,
+                    const uint8_t *src, const mafp_state *ghost, int64_t cap_ghost,
+                    uint8_t *ghost_flag, int32_t *ghost_src, int64_t *n_ghost_dev, void *stream);
+int mafp_ghost_append(mafp_ctx *ctx, int64_t n_regular, int64_t n_ghost, int32_t dtype,
+                      const mafp_state *ghost, const mafp_state *all, int64_t cap_all,
+                      int64_t *n_all_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

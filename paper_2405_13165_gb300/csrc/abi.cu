@@ -33,6 +33,12 @@ int remap_switched(mafp_ctx *, int64_t, int32_t, const mafp_state *, const uint8
                    const int64_t *, const int32_t *, const mafp_state *, int64_t, int32_t *,
                    int64_t *, cudaStream_t);
 void init_kernel_attributes();
+int ghost_sources(mafp_ctx *, int64_t, const uint8_t *, const int64_t *, const int32_t *,
+                  uint8_t *, cudaStream_t);
+int ghost_seed(mafp_ctx *, int64_t, int32_t, const mafp_state *, const uint8_t *,
+               const mafp_state *, int64_t, uint8_t *, int32_t *, int64_t *, cudaStream_t);
+int ghost_append(mafp_ctx *, int64_t, int64_t, int32_t, const mafp_state *, const mafp_state *,
+                 int64_t, int64_t *, cudaStream_t);
 
 int sm_count() {
   static int cached[64] = {0};
@@ -377,6 +383,50 @@ int mafp_build_stencils_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const 
   if (ensure_device(ctx)) return MAFP_ECUDA;
   return build_stencils_backward(ctx, n, dtype, pos_h, model, frame, row_ptr, col, fields, gout,
                                  gpos, (cudaStream_t)stream);
+}
+
+int mafp_ghost_sources(mafp_ctx *ctx, int64_t n, const uint8_t *model, const int64_t *row_ptr,
+                       const int32_t *col, uint8_t *src, void *stream) {
+  if (!ctx) return MAFP_EINVAL;
+  int rc;
+  if ((rc = check_n(ctx, n))) return rc;
+  if (n == 0) return MAFP_OK;
+  REQUIRE(model); REQUIRE(row_ptr); REQUIRE(col); REQUIRE(src);
+  if (ensure_device(ctx)) return MAFP_ECUDA;
+  return ghost_sources(ctx, n, model, row_ptr, col, src, (cudaStream_t)stream);
+}
+
+int mafp_ghost_seed(mafp_ctx *ctx, int64_t n, int32_t dtype, const mafp_state *in,
+                    const uint8_t *src, const mafp_state *ghost, int64_t cap_ghost,
+                    uint8_t *ghost_flag, int32_t *ghost_src, int64_t *n_ghost_dev,
+                    void *stream) {
+  if (!ctx) return MAFP_EINVAL;
+  int rc;
+  if ((rc = check_dtype(ctx, dtype)) || (rc = check_n(ctx, n))) return rc;
+  if (cap_ghost < 0) return fail(ctx, MAFP_EINVAL, "negative cap_ghost");
+  REQUIRE(in); REQUIRE(src); REQUIRE(ghost); REQUIRE(ghost_flag); REQUIRE(ghost_src);
+  if (ensure_device(ctx)) return MAFP_ECUDA;
+  if (n == 0) {
+    if (n_ghost_dev)
+      MAFP_CUDA_TRY(ctx, cudaMemsetAsync(n_ghost_dev, 0, sizeof(int64_t), (cudaStream_t)stream));
+    return MAFP_OK;
+  }
+  return ghost_seed(ctx, n, dtype, in, src, ghost, cap_ghost, ghost_flag, ghost_src,
+                    n_ghost_dev, (cudaStream_t)stream);
+}
+
+int mafp_ghost_append(mafp_ctx *ctx, int64_t n_regular, int64_t n_ghost, int32_t dtype,
+                      const mafp_state *ghost, const mafp_state *all, int64_t cap_all,
+                      int64_t *n_all_dev, void *stream) {
+  if (!ctx) return MAFP_EINVAL;
+  int rc;
+  if ((rc = check_dtype(ctx, dtype)) || (rc = check_n(ctx, n_ghost))) return rc;
+  if (n_regular < 0 || cap_all < n_regular)
+    return fail(ctx, MAFP_EINVAL, "n_regular must lie in [0, cap_all]");
+  REQUIRE(ghost); REQUIRE(all);
+  if (ensure_device(ctx)) return MAFP_ECUDA;
+  return ghost_append(ctx, n_regular, n_ghost, dtype, ghost, all, cap_all, n_all_dev,
+                      (cudaStream_t)stream);
 }
 
 int mafp_remap_switched(mafp_ctx *ctx, int64_t n, int32_t dtype, const mafp_state *in,

@@ -7,33 +7,9 @@
 //  3. survivors copied; 3D -> 2D particles aggregate their set T_i;
 //     2D -> 3D particles split their mass and emit gamma new particles.
 #include "internal.cuh"
+#include "state.cuh"
 
 namespace mafp {
-
-template <typename T>
-struct StateT {
-  vec4_t<T> *pos_h, *vp, *normal;
-  T *rho, *eta, *mass, *diam, *hfilm, *h3d;
-  uint8_t *model, *type, *last;
-};
-
-template <typename T>
-static StateT<T> cast_state(const mafp_state *s) {
-  StateT<T> r;
-  r.pos_h = (vec4_t<T> *)s->pos_h;
-  r.vp = (vec4_t<T> *)s->vp;
-  r.normal = (vec4_t<T> *)s->normal;
-  r.rho = (T *)s->rho;
-  r.eta = (T *)s->eta;
-  r.mass = (T *)s->mass;
-  r.diam = (T *)s->diam;
-  r.hfilm = (T *)s->hfilm;
-  r.h3d = (T *)s->h3d;
-  r.model = s->model;
-  r.type = s->type;
-  r.last = s->last;
-  return r;
-}
 
 __device__ __forceinline__ double dist2_64(double xi, double yi, double zi, double xj, double yj,
                                            double zj) {

@@ -87,6 +87,9 @@ def lib():
         L.mafp_build_neighbours.argtypes = [p, i64, i32, p, p, p, i64, p, p, p]
         L.mafp_build_neighbours_batched.argtypes = [p, i64, i32, i32, p, p, p, p, i64, p, p, p]
         L.mafp_cell_order.argtypes = [p, i64, i32, p, p, p]
+        L.mafp_ghost_sources.argtypes = [p, i64, p, p, p, p, p]
+        L.mafp_ghost_seed.argtypes = [p, i64, i32, p, p, p, i64, p, p, p, p]
+        L.mafp_ghost_append.argtypes = [p, i64, i64, i32, p, p, i64, p, p]
         L.mafp_classify_pca.argtypes = [p, i64, i32] + [p] * 17
         L.mafp_build_stencils.argtypes = [p, i64, i32, p, p, p, p, p, p, p, p, p]
         L.mafp_apply_ops.argtypes = [p, i64, i32, p, p, p, p, p, p]
@@ -102,7 +105,8 @@ def lib():
                      "mafp_build_neighbours", "mafp_build_neighbours_batched", "mafp_cell_order",
                      "mafp_classify_pca", "mafp_build_stencils",
                      "mafp_apply_ops", "mafp_transpose_map", "mafp_apply_ops_backward",
-                     "mafp_build_stencils_backward", "mafp_remap_switched"):
+                     "mafp_build_stencils_backward", "mafp_remap_switched",
+                     "mafp_ghost_sources", "mafp_ghost_seed", "mafp_ghost_append"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -395,3 +399,39 @@ def symbols_declared_in_header(header: str | None = None) -> list[str]:
     header = header or os.path.join(os.path.dirname(_HERE), "include", "mafp.h")
     src = open(header).read()
     return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*(mafp_\w+)\s*\(", src, re.M)))
+
+
+def ghost_sources(ctx: Context, model, row_ptr, col, src, stream=None):
+    """Alg. 5, first loop: src[i] = 1 when S_i holds a particle of the other model."""
+    n = row_ptr.numel() - 1
+    _need(model, "model", torch.uint8, n)
+    _need(row_ptr, "row_ptr", torch.int64, n + 1)
+    _need(col, "col", torch.int32)
+    _need(src, "src", torch.uint8, n)
+    ctx.check(lib().mafp_ghost_sources(ctx.handle, n, _ptr(model), _ptr(row_ptr), _ptr(col),
+                                       _ptr(src), _stream(stream)))
+
+
+def ghost_seed(ctx: Context, n: int, state_in: dict, src, ghost: dict, cap_ghost: int,
+               ghost_flag, ghost_src, n_ghost, dtype=F32_REFINED, stream=None):
+    """Alg. 5, second loop: copies of the sources and the transition each takes."""
+    sin, _a = make_state(state_in, dtype)
+    sg, _b = make_state(ghost, dtype)
+    _need(src, "src", torch.uint8, n)
+    _need(ghost_flag, "ghost_flag", torch.uint8, cap_ghost)
+    _need(ghost_src, "ghost_src", torch.int32, cap_ghost)
+    _need(n_ghost, "n_ghost", torch.int64, 1, allow_none=True)
+    ctx.check(lib().mafp_ghost_seed(ctx.handle, n, dtype, C.byref(sin), _ptr(src), C.byref(sg),
+                                    int(cap_ghost), _ptr(ghost_flag), _ptr(ghost_src),
+                                    _ptr(n_ghost), _stream(stream)))
+
+
+def ghost_append(ctx: Context, n_regular: int, n_ghost: int, ghost: dict, all_: dict,
+                 cap_all: int, n_all, dtype=F32_REFINED, stream=None):
+    """Alg. 5 result: transitioned ghosts appended behind the regular particles."""
+    sg, _a = make_state(ghost, dtype)
+    sa, _b = make_state(all_, dtype)
+    _need(n_all, "n_all", torch.int64, 1, allow_none=True)
+    ctx.check(lib().mafp_ghost_append(ctx.handle, int(n_regular), int(n_ghost), dtype,
+                                      C.byref(sg), C.byref(sa), int(cap_all), _ptr(n_all),
+                                      _stream(stream)))

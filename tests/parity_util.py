@@ -84,12 +84,12 @@ def column_error(a, b):
     return normwise, np.percentile(comp, 99, axis=0) if comp.size else np.zeros(16)
 
 
-def storage_bound(rp, col, coef, fields, rows=None):
-    """Per output element, 2^-24 sum_j |c_ij^op| |u_j - u_i| (FP64 coefficients):
-    what a relative coefficient error of one FP32 unit roundoff can do to that
-    output.  Near-degenerate rows (thin 3D layers, condition 1e3 and up) have
-    large, cancelling coefficients; there an output is this many times more
-    sensitive than its own size suggests."""
+def sensitivity(rp, col, coef, fields, rows=None):
+    """Per output element, sum_j |c_ij^op| |u_j - u_i| (FP64 coefficients): how
+    far a relative coefficient error of 1 can move that output.  Near-degenerate
+    rows (thin 3D layers, condition 1e3 and up) have large, cancelling
+    coefficients, so an output can be far more sensitive than its own size;
+    columns that vanish exactly (d/dz of a depth-constant field) likewise."""
     n = len(rp) - 1
     F = np.asarray(fields, np.float64)
     rows_of = np.repeat(np.arange(n), np.diff(rp))
@@ -100,19 +100,20 @@ def storage_bound(rp, col, coef, fields, rows=None):
     for f in range(4):
         for op in range(4):
             b[:, f, op] = np.bincount(r, c[:, op] * du[:, f], minlength=n)
-    return b * 2.0 ** -24
+    return b
 
 
-# Refined FP32 stencils agree with FP64 to ~1e-6 of a row's largest coefficient
-# (about 16 unit roundoffs: measured 1e-6 .. 3.5e-6 up to condition 1e5); an
-# output inherits that times its sensitivity.  32 roundoffs leaves 2x margin.
-COEF_ROUNDOFFS = 32.0
+# Relative coefficient error each path leaves: refined FP32 stencils agree with
+# FP64 to ~1e-6 of a row's largest coefficient (about 16 unit roundoffs:
+# measured 1e-6 .. 3.5e-6 up to condition 1e5; 32 leaves 2x margin); the FP64
+# path is held to its stencil bar.
+COEF_REL = {M.F32_REFINED: 32.0 * 2.0 ** -24, M.F32_PLAIN: 2e-3, M.F64: 1e-10}
 
 
-def outputs_within(a, b, bound, tol):
-    """|a - b| <= tol * (column max of |b|) + COEF_ROUNDOFFS * bound, elementwise;
+def outputs_within(a, b, sens, tol, coef_rel):
+    """|a - b| <= tol * (column max of |b|) + coef_rel * sens, elementwise;
     returns the worst ratio of the error to that allowance (<= 1 passes)."""
     scale = np.abs(b).reshape(-1, 16).max(0)
-    allow = tol * scale + COEF_ROUNDOFFS * bound.reshape(-1, 16)
+    allow = tol * scale + coef_rel * sens.reshape(-1, 16)
     err = np.abs(a - b).reshape(-1, 16)
     return float((err / np.where(allow > 0, allow, 1e-300)).max()) if err.size else 0.0

@@ -16,7 +16,7 @@ if not torch.cuda.is_available():
 import oracle as O  # noqa: E402
 import tray_oracle as TO  # noqa: E402
 from paper_2405_13165_gb300 import mafp as M, tray  # noqa: E402
-from parity_util import TOL, outputs_within, storage_bound  # noqa: E402
+from parity_util import COEF_REL, TOL, outputs_within, sensitivity  # noqa: E402
 
 
 def _pairs(rp, col):
@@ -63,9 +63,9 @@ def test_tray_trajectory_matches_oracle_trajectory(orc):
         # coefficients: an FP32-refined coefficient error of ~1e-6 of the row's
         # largest coefficient moves such an output beyond 1e-4 of its column, so
         # that sensitivity is allowed on top of the normwise bar
-        bound = storage_bound(info["row_ptr"], info["col"], info["coef"], s["vp"])
-        worst = outputs_within(p.out[:n].double().cpu().numpy(), info["out"], bound,
-                               TOL[M.F32_REFINED])
+        sens = sensitivity(info["row_ptr"], info["col"], info["coef"], s["vp"])
+        worst = outputs_within(p.out[:n].double().cpu().numpy(), info["out"], sens,
+                               TOL[M.F32_REFINED], COEF_REL[M.F32_REFINED])
         assert worst <= 1.0, (k, worst)
         assert st["n_out"] == info["n_out"]
         np.testing.assert_array_equal(loop.old2new[:n].cpu().numpy(), info["old2new"])
@@ -109,9 +109,9 @@ def test_tray_full_size_twenty_steps(orc):
     rows = np.sort(np.random.default_rng(55).choice(n0, n0 // 100, replace=False))
     coef, status, _ = O.stencils(c.pos_h, c.model, rp, col, rows=rows)
     out = O.apply(rp, col, coef, c.vp, rows=rows)
-    bound = storage_bound(rp, col, coef, c.vp, rows=rows)
-    worst = outputs_within(p.out[:n0].double().cpu().numpy()[rows], out[rows], bound[rows],
-                           TOL[M.F32_REFINED])
+    sens = sensitivity(rp, col, coef, c.vp, rows=rows)
+    worst = outputs_within(p.out[:n0].double().cpu().numpy()[rows], out[rows], sens[rows],
+                           TOL[M.F32_REFINED], COEF_REL[M.F32_REFINED])
     assert worst <= 1.0, worst
     # twenty steps: invariants at every step
     stats = [st]
