@@ -335,7 +335,7 @@ int mafp_profile_read(mafp_ctx *ctx, mafp_kernel_time *out, int32_t cap, int32_t
  * Buffer zone of Sec. 5.3 (Alg. 5), in three calls around a transition of the
  * ghost cloud:
  *  mafp_ghost_sources -- first loop: src[i] = 1 when S_i (Eq. Nbd, all models;
- *    the "within h" of Sec. 5.3 read as the neighbourhood) holds a particle of
+ *    the distance h of Sec. 5.3 read as the neighbourhood) holds a particle of
  *    the other model, else 0.  src uint8 [n] written.
  *  mafp_ghost_seed -- second loop: every source is copied, in index order, as
  *    an intermediate ghost of the same model at the same place (last = 0);
