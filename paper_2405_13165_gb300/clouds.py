@@ -458,6 +458,36 @@ def interface_strip(dx: float = 0.02, layers: int = 3, extent=(1.0, 0.5), x_spli
     return c
 
 
+# --------------------------------------------------- advection-diffusion plate
+ADV_DISC = (0.5, 0.5, 0.2)        # (x0, y0, radius) of the initial hot disc (Sec. 7.2)
+
+
+def advection_plate(h: float, extent=(4.0, 3.0), seed: int = SEED_BASE + 7) -> Cloud:
+    """The advection-diffusion plate of Sec. 7.2, all film (2D) at the start:
+    film particles on [0, 4] x [0, 3] at spacing dx = h / 3.5 with film height
+    2 dx (a film particle lifted to 3D by Alg. 4 becomes a column of three),
+    temperature T in the first field slot: 1 inside the disc ADV_DISC, else 0
+    (constant through the depth); the other field slots are 0."""
+    dx = h / 3.5
+    rng = np.random.default_rng(seed)
+    ni, nj = int(round(extent[0] / dx)), int(round(extent[1] / dx))
+    I, J = np.meshgrid(np.arange(ni), np.arange(nj), indexing="ij")
+    xyz = np.stack([(I.ravel() + 0.5) * dx, (J.ravel() + 0.5) * dx, np.zeros(I.size)], 1)
+    n = xyz.shape[0]
+    model = np.full(n, MODEL_2D, np.uint8)
+    ptype = np.full(n, TYPE_WALL, np.uint8)
+    normal = np.zeros((n, 4), np.float32)
+    normal[:, 2] = 1.0
+    xyz = _jitter(xyz, np.ones(n, bool), dx, rng)
+    c = _finish(xyz, model, ptype, normal, 2.0 * dx, dx, rng, f"advection_plate(h={h:g})")
+    x0, y0, r = ADV_DISC
+    P = c.pos_h.astype(np.float64)
+    inside = (P[:, 0] - x0) ** 2 + (P[:, 1] - y0) ** 2 <= r * r
+    c.vp = np.zeros((n, 4), np.float32)
+    c.vp[:, 0] = inside.astype(np.float32)
+    return c
+
+
 # ---------------------------------------------------------------- tray loop
 TRAY_SHEET = (2.0, 1.0)          # film sheet extent (m)
 TRAY_JET_FOOT = (0.45, 0.5)      # where the jet axis meets the plate
