@@ -32,8 +32,8 @@ __device__ __forceinline__ void add_xyz<double>(double *p, double x, double y, d
   atomicAdd(p + 2, z);
 }
 
-// neighbours a lane gathers ahead of use in the moment, lbar and gradient passes
-constexpr int kGradGatherA = 4, kGradGatherB = 2, kGradGatherC = 2;
+// neighbours a lane gathers ahead of use in the moment / lbar pass and the gradient pass
+constexpr int kGradGatherA = 2, kGradGatherC = 2;
 
 // Returns 0 done, 1 no gradient (deficient), 2 queued for the FP64 redo.
 template <typename TS, typename C, int M, int G, bool QUEUE>
@@ -59,60 +59,6 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
     t2[2] = n0 * t1[1] - n1 * t1[0];
   }
   const long long b = row_ptr[i], e1 = row_ptr[i + 1];
-  // ---- moments and factor (as in the forward build)
-  C A[VA];
-#pragma unroll
-  for (int k = 0; k < VA; ++k) A[k] = C(0);
-  int cnt = 0;
-  for (long long e0 = b + lane; e0 < e1; e0 += kGradGatherA * G) {
-    V xs[kGradGatherA];
-    bool oks[kGradGatherA];
-    gather_row<kGradGatherA, G>(e0, e1, i, mi, col, pos, model, xs, oks);
-#pragma unroll
-    for (int u = 0; u < kGradGatherA; ++u) {
-      C p[M];
-      C w = basis_at<M, C>(xi, xs[u], hinv, t1, t2, sp, p);
-      w = oks[u] ? w : C(0);   // other model / past the row end: contributes exact zeros
-      cnt += oks[u] ? 1 : 0;
-#pragma unroll
-      for (int r = 0; r < M; ++r) {
-        const C wp = w * p[r];
-#pragma unroll
-        for (int c = 0; c <= r; ++c) A[pk(r, c)] += wp * p[c];
-      }
-    }
-  }
-  cnt = group_sum<G>(cnt);
-  reduce_scatter<G, VA>(A);
-  __syncwarp(gm);
-#pragma unroll
-  for (int k = 0; k < VA / G; ++k) sm[lane * (VA / G) + k] = A[k];
-  __syncwarp(gm);
-  C L[NA];
-#pragma unroll
-  for (int k = 0; k < NA; ++k) L[k] = sm[k];
-  __syncwarp(gm);
-  C tr = 0;
-#pragma unroll
-  for (int r = 0; r < M; ++r) tr += L[pk(r, r)];
-  C invd[M], pmin, pmax;
-  const bool ok = (cnt >= M) && cholesky<M, C>(L, invd, sp.piv_tol_rel * tr, pmin, pmax);
-  const C cond = (pmax / pmin) * (pmax / pmin);
-  if (!ok || (QUEUE && !(cond <= sp.cond_max))) return (QUEUE && cnt >= M) ? 2 : 1;
-  C *Ls = sm + StSmem<M, G>::SCR;
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < NA; ++k) Ls[k] = L[k];
-  }
-  __syncwarp(gm);
-  C lam[NR][M];
-#pragma unroll
-  for (int k = 0; k < NR; ++k) {
-    C bb[M];
-#pragma unroll
-    for (int r = 0; r < M; ++r) bb[r] = rhs<M, C>(k, r);
-    chol_solve_s<M, C>(Ls, invd, bb, lam[k]);
-  }
   // per-operator output scale of the forward kernel: gradient 1/h, Laplacian 1/h^2
   const C h2inv = hinv * hinv;
   const V fi = ld4(fields + i);
@@ -138,35 +84,77 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
       gb[2] = g4[3] * h2inv;
     }
   };
-  // ---- pass 1: lbar_k = sum_j gbar_jk w_j p_j, then mu_k = A^-1 lbar_k
-  {
-    C R[VR];
+  // ---- one pass: moments A = sum_j w_j p_j p_j^T and lbar_k = sum_j gbar_jk w_j p_j
+  // (gbar depends on the fields only, so it needs no solution yet)
+  C A[VA];
 #pragma unroll
-    for (int k = 0; k < VR; ++k) R[k] = C(0);
-    for (long long e0 = b + lane; e0 < e1; e0 += kGradGatherB * G) {
-      V xs[kGradGatherB], fs[kGradGatherB];
-      int js[kGradGatherB];
-      bool oks[kGradGatherB];
-      gather_row_f<kGradGatherB, G>(e0, e1, i, mi, col, pos, model, fields, xs, fs, js, oks);
+  for (int k = 0; k < VA; ++k) A[k] = C(0);
+  C R[VR];
 #pragma unroll
-      for (int u = 0; u < kGradGatherB; ++u) {
-        C p[M], gb[NR];
-        C w = basis_at<M, C>(xi, xs[u], hinv, t1, t2, sp, p);
-        w = oks[u] ? w : C(0);
-        gbar(fs[u], gb);
+  for (int k = 0; k < VR; ++k) R[k] = C(0);
+  int cnt = 0;
+  for (long long e0 = b + lane; e0 < e1; e0 += kGradGatherA * G) {
+    V xs[kGradGatherA], fs[kGradGatherA];
+    int js[kGradGatherA];
+    bool oks[kGradGatherA];
+    gather_row_f<kGradGatherA, G>(e0, e1, i, mi, col, pos, model, fields, xs, fs, js, oks);
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-          const C gw = gb[k] * w;
+    for (int u = 0; u < kGradGatherA; ++u) {
+      C p[M], gb[NR];
+      C w = basis_at<M, C>(xi, xs[u], hinv, t1, t2, sp, p);
+      w = oks[u] ? w : C(0);   // other model / past the row end: contributes exact zeros
+      cnt += oks[u] ? 1 : 0;
 #pragma unroll
-          for (int r = 0; r < M; ++r) R[k * M + r] += gw * p[r];
-        }
+      for (int r = 0; r < M; ++r) {
+        const C wp = w * p[r];
+#pragma unroll
+        for (int c = 0; c <= r; ++c) A[pk(r, c)] += wp * p[c];
+      }
+      gbar(fs[u], gb);
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        const C gw = gb[k] * w;
+#pragma unroll
+        for (int r = 0; r < M; ++r) R[k * M + r] += gw * p[r];
       }
     }
-    reduce_scatter<G, VR>(R);
-#pragma unroll
-    for (int k = 0; k < VR / G; ++k) sm[lane * (VR / G) + k] = R[k];
-    __syncwarp(gm);
   }
+  cnt = group_sum<G>(cnt);
+  reduce_scatter<G, VA>(A);
+  reduce_scatter<G, VR>(R);
+  __syncwarp(gm);
+#pragma unroll
+  for (int k = 0; k < VA / G; ++k) sm[lane * (VA / G) + k] = A[k];
+  __syncwarp(gm);
+  C L[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) L[k] = sm[k];
+  __syncwarp(gm);
+#pragma unroll
+  for (int k = 0; k < VR / G; ++k) sm[lane * (VR / G) + k] = R[k];
+  __syncwarp(gm);
+  C tr = 0;
+#pragma unroll
+  for (int r = 0; r < M; ++r) tr += L[pk(r, r)];
+  C invd[M], pmin, pmax;
+  const bool ok = (cnt >= M) && cholesky<M, C>(L, invd, sp.piv_tol_rel * tr, pmin, pmax);
+  const C cond = (pmax / pmin) * (pmax / pmin);
+  if (!ok || (QUEUE && !(cond <= sp.cond_max))) return (QUEUE && cnt >= M) ? 2 : 1;
+  C *Ls = sm + StSmem<M, G>::SCR;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NA; ++k) Ls[k] = L[k];
+  }
+  __syncwarp(gm);
+  C lam[NR][M];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    C bb[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) bb[r] = rhs<M, C>(k, r);
+    chol_solve_s<M, C>(Ls, invd, bb, lam[k]);
+  }
+  // ---- mu_k = A^-1 lbar_k
   C mu[NR][M];
 #pragma unroll
   for (int k = 0; k < NR; ++k) {
