@@ -487,6 +487,8 @@ __global__ void k_check_nnz(const long long *row_ptr, int64_t n, long long cap_n
 // The expand kernel turns the bits back into column indices, so the distance
 // tests run once.
 constexpr int kMaskThreads = 64;
+constexpr int kMaskTile = kMaskCap + kMaskWords;   // candidates plus one pad per word
+constexpr int kMaskMaxP = 512;                     // particles of one cell in the mask kernel
 constexpr int kExpThreads = 128;
 constexpr int kExpChunk = 64;             // particles of a cell expanded per round
 
@@ -543,6 +545,8 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *cand = reinterpret_cast<V *>(smem_raw);
   __shared__ int r_lo[9], r_len[9], r_off[10];
+  __shared__ int cnt_s[kMaskMaxP];
+  __shared__ int s_ovf;
   if (!cg.all->ok) return;
   const int tid = threadIdx.x;
   const int nu = *n_ucell;
@@ -558,56 +562,70 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
         o += r_len[r];
       }
       r_off[9] = o;
-      if (o > kMaskCap) overflow[atomicAdd(n_overflow, 1)] = cb;
+      // too many candidates for the tile, or too many particles for the
+      // per-particle counters: the warp-per-particle kernel takes the cell
+      s_ovf = (o > kMaskCap || s1 - s0 > kMaskMaxP) ? 1 : 0;
+      if (s_ovf) overflow[atomicAdd(n_overflow, 1)] = cb;
     }
     __syncthreads();
     const int total = r_off[9];
-    if (total <= kMaskCap) {
+    if (!s_ovf) {
+      // the tile holds candidate c at slot c + c / 32: one pad entry per word
+      // puts the words that different threads test in different banks
       for (int r = 0; r < 9; ++r)
-        for (int t = tid; t < r_len[r]; t += kMaskThreads) cand[r_off[r] + t] = ld4(spos + r_lo[r] + t);
+        for (int t = tid; t < r_len[r]; t += kMaskThreads) {
+          const int c = r_off[r] + t;
+          cand[c + (c >> 5)] = ld4(spos + r_lo[r] + t);
+        }
+      const int P = s1 - s0;
+      for (int q = tid; q < P; q += kMaskThreads) cnt_s[q] = 0;
       __syncthreads();
       const int nwords = (total + 31) >> 5;
-      for (int p0 = s0; p0 < s1; p0 += kMaskThreads) {
-        const int p = p0 + tid;
-        const bool active = p < s1;
-        const V xi = ld4(spos + (active ? p : s0));
-        int cnt = 0;
-        for (int w = 0; w < nwords; ++w) {
-          const int base = w << 5;
-          const uint32_t valid = (total - base) >= 32 ? 0xffffffffu : ((1u << (total - base)) - 1u);
-          uint32_t m = 0, band = 0;
-          if constexpr (sizeof(T) == 4) {
-            // branch-free FP32 test of 32 candidates; the tile always holds
-            // 32 * nwords <= kMaskCap entries, so reads past `total` stay in it
+      const int own = r_off[4] + (s0 - r_lo[4]);   // the cell's own particles, in run 4
+      // one work item = (word, particle); consecutive threads take consecutive
+      // particles of a word, so small cells still fill the block
+      const int items = P * nwords;
+      for (int it = tid; it < items; it += kMaskThreads) {
+        const int w = it / P, q = it - w * P;
+        const int oc = own + q;
+        const V xi = cand[oc + (oc >> 5)];
+        const int base = w << 5;
+        const V *cw = cand + base + w;           // slot of candidate 32 w
+        const uint32_t valid = (total - base) >= 32 ? 0xffffffffu : ((1u << (total - base)) - 1u);
+        uint32_t m = 0, band = 0;
+        if constexpr (sizeof(T) == 4) {
+          // branch-free FP32 test of 32 candidates; the tile always holds
+          // 32 * nwords <= kMaskCap entries (plus pads), so reads past `total`
+          // stay in it and are masked off
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-              const float4 b = cand[base + k];
-              const float dx = b.x - xi.x, dy = b.y - xi.y, dz = b.z - xi.z;
-              const float d2 = (dx * dx + dy * dy) + dz * dz;
-              const float r = (xi.w + b.w) * 0.5f;
-              const float r2 = r * r;
-              m |= (d2 < r2 * 0.99999f ? 1u : 0u) << k;
-              band |= (d2 <= r2 * 1.00001f ? 1u : 0u) << k;
-            }
-            m &= valid;
-            band &= valid & ~m;
-            // pairs within 1e-5 of the bound: the FP64 definition decides
-            while (band) {
-              const int k = __ffs(band) - 1;
-              band &= band - 1;
-              const float4 b = cand[base + k];
-              if (in_support64(xi.x, xi.y, xi.z, xi.w, b.x, b.y, b.z, b.w)) m |= 1u << k;
-            }
-          } else {
-            for (int k = 0; k < 32; ++k)
-              if ((valid >> k) & 1u)
-                if (support_test(xi, cand[base + k])) m |= 1u << k;
+          for (int k = 0; k < 32; ++k) {
+            const float4 b = cw[k];
+            const float dx = b.x - xi.x, dy = b.y - xi.y, dz = b.z - xi.z;
+            const float d2 = (dx * dx + dy * dy) + dz * dz;
+            const float r = (xi.w + b.w) * 0.5f;
+            const float r2 = r * r;
+            m |= (d2 < r2 * 0.99999f ? 1u : 0u) << k;
+            band |= (d2 <= r2 * 1.00001f ? 1u : 0u) << k;
           }
-          if (active) mask[(int64_t)w * stride + p] = m;
-          cnt += __popc(m);
+          m &= valid;
+          band &= valid & ~m;
+          // pairs within 1e-5 of the bound: the FP64 definition decides
+          while (band) {
+            const int k = __ffs(band) - 1;
+            band &= band - 1;
+            const float4 b = cw[k];
+            if (in_support64(xi.x, xi.y, xi.z, xi.w, b.x, b.y, b.z, b.w)) m |= 1u << k;
+          }
+        } else {
+          for (int k = 0; k < 32; ++k)
+            if ((valid >> k) & 1u)
+              if (support_test(xi, cw[k])) m |= 1u << k;
         }
-        if (active) counts[svals[p]] = cnt;
+        mask[(int64_t)w * stride + s0 + q] = m;
+        atomicAdd(&cnt_s[q], __popc(m));
       }
+      __syncthreads();
+      for (int q = tid; q < P; q += kMaskThreads) counts[svals[s0 + q]] = cnt_s[q];
     }
     __syncthreads();
   }
@@ -641,7 +659,7 @@ __global__ void __launch_bounds__(kExpThreads) k_nbr_expand(
     }
     __syncthreads();
     const int total = r_off[9];
-    if (total <= kMaskCap) {
+    if (total <= kMaskCap && s1 - s0 <= kMaskMaxP) {   // the mask kernel's cells
       for (int r = 0; r < 9; ++r)
         for (int t = tid; t < r_len[r]; t += kExpThreads) cand_v[r_off[r] + t] = svals[r_lo[r] + t];
       const int nwords = (total + 31) >> 5;
@@ -817,7 +835,7 @@ static int build_neighbours_t(mafp_ctx *ctx, int64_t n, int nb, const long long 
   int32_t *n_overflow = ctx->n_ucell + 1;
   const int64_t stride = ctx->cap_particles;
   MAFP_TIMED(ctx, s, sizeof(T) == 4 ? "k_nbr_mask<float>" : "k_nbr_mask<double>",
-             k_nbr_mask<T><<<sms * 16, kMaskThreads, kMaskCap * sizeof(V), s>>>(
+             k_nbr_mask<T><<<sms * 16, kMaskThreads, kMaskTile * sizeof(V), s>>>(
                  cg, ctx->ucell, ctx->n_ucell, spos, vin, ctx->cell_start,
                  ctx->cell_end, ctx->counts, ctx->nbr_mask, stride, ctx->overflow, n_overflow));
   MAFP_TIMED(ctx, s, "k_nbr<T,false>(overflow cells)",
@@ -882,9 +900,9 @@ int build_neighbours_batched(mafp_ctx *ctx, int64_t n, int32_t dtype, int32_t nc
 
 void init_kernel_attributes() {
   cudaFuncSetAttribute(k_nbr_mask<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kMaskCap * (int)sizeof(float4));
+                       kMaskTile * (int)sizeof(float4));
   cudaFuncSetAttribute(k_nbr_mask<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kMaskCap * (int)sizeof(double4_16a));
+                       kMaskTile * (int)sizeof(double4_16a));
   cudaFuncSetAttribute(k_nbr<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kNbrSmemBytes);
   cudaFuncSetAttribute(k_nbr<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
