@@ -139,8 +139,12 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle
 def cpu_oracle_sample(cloud, m: int):
-    """Run the FP64 oracle pipeline on the first m particles (cell order) of
-    the cloud; returns (seconds, threads, description)."""
+    """The FP64 oracle on the step's stages: neighbours, detection, smoothing,
+    remap, stencils, apply and apply transpose on the first m particles (cell
+    order; m = the whole cloud by default), and the single-threaded stencil
+    adjoint on a seeded 5 % of the rows (the oracle skips rows whose output
+    gradient is zero), its time scaled by 20.  Returns (seconds for the whole
+    sample, threads, description, particles)."""
     import oracle
     sub = cloud.take(np.arange(min(m, cloud.n)))
     t0 = time.perf_counter()
@@ -152,10 +156,18 @@ def cpu_oracle_sample(cloud, m: int):
     coef, status, cond = oracle.stencils(sub.pos_h, sub.model, rp, col)
     out = oracle.apply(rp, col, coef, sub.vp)
     oracle.apply_T(rp, col, coef, out)
-    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    G = np.zeros_like(out)
+    rows = np.random.default_rng(5).random(sub.n) < 0.05
+    G[rows] = out[rows]
+    oracle.stencil_grad(sub.pos_h, sub.model, rp, col, sub.vp, G)
+    t2 = time.perf_counter()
+    dt = (t1 - t0) + (t2 - t1) / 0.05
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    desc = (f"first {sub.n} particles (cell order) of the same cloud; oracle neighbours, "
-            f"detection, smoothing, remap, stencils, apply, apply transpose in FP64")
+    desc = (f"first {sub.n} particles (cell order) of the same cloud: oracle neighbours, "
+            f"detection, smoothing, remap, stencils, apply, apply transpose in FP64 "
+            f"({t1 - t0:.1f} s, OpenMP); stencil adjoint single-threaded on a seeded 5 % of "
+            f"the rows ({t2 - t1:.1f} s, scaled x20)")
     return dt, threads, desc, sub.n
 
 
