@@ -118,7 +118,7 @@ __device__ double hfilm64(int64_t i, const V *pos, const uint8_t *model, const u
 }
 
 template <typename T, int G>
-__global__ void __launch_bounds__(kClsThreads) k_classify(
+__global__ void __launch_bounds__(kClsThreads, sizeof(T) == 4 ? 8 : 1) k_classify(
     int64_t n, const vec4_t<T> *pos, const uint8_t *model, const uint8_t *type,
     const vec4_t<T> *normal, const T *vol, const T *h3d, const uint8_t *user,
     const long long *row_ptr, const int32_t *col, uint8_t *preflag, vec4_t<T> *eig,
