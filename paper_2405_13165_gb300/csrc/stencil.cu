@@ -188,7 +188,7 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
 
 // Main kernel: every particle of model (M == 10 ? 3D : 2D).
 template <typename TS, typename C, int M, int G, bool REFINE, bool QUEUE>
-__global__ void __launch_bounds__(kStThreads, 4) k_stencil(
+__global__ void __launch_bounds__(kStThreads, M == 10 ? 4 : 6) k_stencil(
     int64_t n, const vec4_t<TS> *pos, const uint8_t *model, const vec4_t<TS> *frame,
     const long long *row_ptr, const int32_t *col, vec4_t<TS> *coef, uint8_t *status,
     float *cond, StParams<C> sp, DevStatus *st, int32_t *queue) {
