@@ -224,9 +224,13 @@ def bench_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     have_bwd = True
+    dsrc = d
 
-    def step(ev=None):
+    def step(ev=None, src=None):
         nonlocal have_bwd
+        d = dsrc if src is None else src
+        sin = state_in if src is None else {**{k: src[k] for k in state_in if k != "type"},
+                                            "type": src["ptype"]}
         marks = []
         def mark():
             if ev is not None:
@@ -238,7 +242,7 @@ def bench_gpu(args):
         mark()
         pipe.classify(d)
         mark()
-        M.remap_switched(ctx, n, state_in, pipe.flag[:n], pipe.row_ptr[: n + 1], pipe.col,
+        M.remap_switched(ctx, n, sin, pipe.flag[:n], pipe.row_ptr[: n + 1], pipe.col,
                          state_out, cap_out, old2new, n_out, dtype)
         mark()
         pipe.stencils(d)
@@ -437,15 +441,19 @@ def bench_gpu(args):
                 "build_particles_per_s_fp64": round(n / (t64 * 1e-3), 1)}
         del pipe64, d64
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step
+    # copies the cloud in from pinned host memory, runs the whole step
+    # (forward, remap, adjoints) and copies derivatives, flags, the remapped
+    # count and both gradients back
     e2e = None
     if not args.no_e2e:
-        keys = ("pos_h", "model", "ptype", "normal", "vol", "h3d", "user", "last", "fields")
+        keys = [k for k in d if k != "vp"]
         host = {k: d[k].cpu().pin_memory() for k in keys}
-        out_host = torch.empty((n, 4, 4), dtype=torch.float32).pin_memory()
-        flag_host = torch.empty(n, dtype=torch.uint8).pin_memory()
+        outs = {"out": pipe.out[:n], "flag": pipe.flag[:n], "n_out": n_out,
+                "gfields": gfields, "gpos": gpos}
+        back = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outs.items()}
         h2d = sum(v.numel() * v.element_size() for v in host.values())
-        d2h = out_host.numel() * 4 + flag_host.numel()
+        d2h = sum(v.numel() * v.element_size() for v in back.values())
         dd = {k: torch.empty_like(d[k]) for k in keys}
         dd["vp"] = dd["fields"]
         tot = 0.0
@@ -455,9 +463,9 @@ def bench_gpu(args):
             e0.record(stream)
             for k in keys:
                 dd[k].copy_(host[k], non_blocking=True)
-            pipe.step(dd)
-            out_host.copy_(pipe.out[:n], non_blocking=True)
-            flag_host.copy_(pipe.flag[:n], non_blocking=True)
+            step(src=dd)
+            for k, v in outs.items():
+                back[k].copy_(v, non_blocking=True)
             e1.record(stream)
             torch.cuda.synchronize()
             if it > 0:
@@ -466,8 +474,9 @@ def bench_gpu(args):
         e2e = {"value": round(world * n / (e2e_ms * 1e-3), 1), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": round(e2e_ms, 3),
-               "path": "pinned host -> device copies, neighbours+detection+stencils+apply, "
-                       "device -> pinned host of derivatives and flags"}
+               "path": "pinned host -> device copies of the cloud, the whole step (neighbours, "
+                       "detection, remap, stencils, apply, both adjoints), device -> pinned host "
+                       "of derivatives, flags, remapped count and gradients"}
 
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
