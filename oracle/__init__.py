@@ -341,3 +341,50 @@ def ghost_zone(state: dict, row_ptr, col, prm=None):
     union = {k: np.concatenate([np.asarray(state[k]), np.asarray(out[k])[keep].astype(
         np.asarray(state[k]).dtype)]) for k in state}
     return union, src, gflag, idx.size
+
+
+def film_momentum(model, vp, rho, eta, hfilm, normal, out, gravity, dt):
+    """Eq. FilmMomentum, one explicit step for the 2D particles in FP64:
+    v + dt (-eta / (rho H^2) v - grad p / rho + g_par), g_par = g - (g.n) n, then
+    projected onto the tangent plane; grad p = out[i, 3, :3].  Particles with
+    H <= 0 and 3D particles keep their velocity.  Returns the new vp."""
+    vp = np.array(vp, np.float64)
+    model = np.asarray(model)
+    H = np.asarray(hfilm, np.float64)
+    live = (model == 1) & (H > 0)
+    n = np.asarray(normal, np.float64)[:, :3]
+    r = np.asarray(rho, np.float64)
+    e = np.asarray(eta, np.float64)
+    gp = np.asarray(out, np.float64).reshape(-1, 4, 4)[:, 3, :3]
+    g = np.asarray(gravity, np.float64)
+    gpar = g[None, :] - (n @ g)[:, None] * n
+    Hs = np.where(live, H, 1.0)
+    v = vp[:, :3] + dt * (-(e / (r * Hs * Hs))[:, None] * vp[:, :3] - gp / r[:, None] + gpar)
+    v = v - (v * n).sum(1)[:, None] * n
+    vp[live, :3] = v[live]
+    return vp
+
+
+def plane_flux(pos_old, pos_new, mass, rho, point, normal):
+    """Volume crossing a plane over one step (Eq. InstFlux as a sum over
+    particles): + m/rho for a signed distance going from < 0 to >= 0, - m/rho
+    back.  Returns (volume, crossings)."""
+    c = np.asarray(point, np.float64)
+    m = np.asarray(normal, np.float64)
+    da = (np.asarray(pos_old, np.float64)[:, :3] - c) @ m
+    db = (np.asarray(pos_new, np.float64)[:, :3] - c) @ m
+    vol = np.asarray(mass, np.float64) / np.asarray(rho, np.float64)
+    up = (da < 0) & (db >= 0)
+    down = (da >= 0) & (db < 0)
+    return float(vol[up].sum() - vol[down].sum()), int(up.sum() + down.sum())
+
+
+def normal_stress(select, out, eta, normal):
+    """Sum over the selected particles of n^T S n = 2 eta n^T (grad v) n with
+    (grad v)_ab = out[i, a, b] (a = velocity component, b = derivative
+    direction).  Returns (sum, count)."""
+    sel = np.asarray(select).astype(bool)
+    G = np.asarray(out, np.float64).reshape(-1, 4, 4)[sel, :3, :3]
+    n = np.asarray(normal, np.float64)[sel, :3]
+    q = np.einsum("ia,iab,ib->i", n, G, n)
+    return float((2.0 * np.asarray(eta, np.float64)[sel] * q).sum()), int(sel.sum())
