@@ -362,6 +362,39 @@ int mafp_ghost_append(mafp_ctx *ctx, int64_t n_regular, int64_t n_ghost, int32_t
                       const mafp_state *ghost, const mafp_state *all, int64_t cap_all,
                       int64_t *n_all_dev, void *stream);
 
+/* --------------------------------------------------------------------------
+ * mafp_film_momentum -- explicit update of the film model's momentum balance
+ * (Eq. FilmMomentum, Sec. 2.2) for every 2D particle:
+ *   v <- v + dt (-eta / (rho H^2) v - grad p / rho + g_par),  g_par = g - (g.n) n,
+ * then v is projected onto the tangent plane (n = the particle's normal).
+ * grad p is taken from `out` (mafp_apply_ops output x4 [4n]: out[4i+3] =
+ * (d/dx, d/dy, d/dz, Lap) of field 3, the pressure slot of vp).  vp x4 [n] is
+ * updated in place (u, v, w; p untouched); H = hfilm; particles with H <= 0
+ * and 3D particles are left alone.  gravity: 3 doubles on the HOST. */
+int mafp_film_momentum(mafp_ctx *ctx, int64_t n, int32_t dtype, const uint8_t *model, void *vp,
+                       const void *rho, const void *eta, const void *hfilm, const void *normal,
+                       const void *out, const double *gravity, double dt, void *stream);
+
+/* mafp_plane_flux -- fluid volume through a plane over one step (Eq. InstFlux
+ * times dt, Sec. 7.3, as a sum over crossing particles): a particle whose
+ * signed distance to the plane (point, unit normal: 3 doubles each, HOST) goes
+ * from < 0 at pos_old to >= 0 at pos_new adds its volume mass/rho, one going
+ * back subtracts it.  acc_dev double [2] (DEVICE) accumulates (volume, number
+ * of crossings); the caller zeroes it. */
+int mafp_plane_flux(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_old,
+                    const void *pos_new, const void *mass, const void *rho, const double *point,
+                    const double *normal, double *acc_dev, void *stream);
+
+/* mafp_normal_stress -- the wall-normal viscous stress of Sec. 7.3,
+ * n^T S n = 2 eta n^T (grad v) n with S = eta (grad v + grad v^T), from the
+ * applied gradients of the velocity fields (out[4i+a] = d v_a / d(x,y,z),
+ * a = 0..2), summed over the particles with select[i] != 0:
+ * acc_dev double [2] (DEVICE) accumulates (sum, count); the region average is
+ * sum / count.  The caller zeroes acc_dev. */
+int mafp_normal_stress(mafp_ctx *ctx, int64_t n, int32_t dtype, const uint8_t *select,
+                       const void *out, const void *eta, const void *normal, double *acc_dev,
+                       void *stream);
+
 #ifdef __cplusplus
 }
 #endif

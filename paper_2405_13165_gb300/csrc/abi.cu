@@ -35,6 +35,13 @@ int remap_switched(mafp_ctx *, int64_t, int32_t, const mafp_state *, const uint8
 void init_kernel_attributes();
 int ghost_sources(mafp_ctx *, int64_t, const uint8_t *, const int64_t *, const int32_t *,
                   uint8_t *, cudaStream_t);
+int film_momentum(mafp_ctx *, int64_t, int32_t, const uint8_t *, void *, const void *,
+                  const void *, const void *, const void *, const void *, const double *, double,
+                  cudaStream_t);
+int plane_flux(mafp_ctx *, int64_t, int32_t, const void *, const void *, const void *,
+               const void *, const double *, const double *, double *, cudaStream_t);
+int normal_stress(mafp_ctx *, int64_t, int32_t, const uint8_t *, const void *, const void *,
+                  const void *, double *, cudaStream_t);
 int ghost_seed(mafp_ctx *, int64_t, int32_t, const mafp_state *, const uint8_t *,
                const mafp_state *, int64_t, uint8_t *, int32_t *, int64_t *, cudaStream_t);
 int ghost_append(mafp_ctx *, int64_t, int64_t, int32_t, const mafp_state *, const mafp_state *,
@@ -383,6 +390,50 @@ int mafp_build_stencils_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const 
   if (ensure_device(ctx)) return MAFP_ECUDA;
   return build_stencils_backward(ctx, n, dtype, pos_h, model, frame, row_ptr, col, fields, gout,
                                  gpos, (cudaStream_t)stream);
+}
+
+int mafp_film_momentum(mafp_ctx *ctx, int64_t n, int32_t dtype, const uint8_t *model, void *vp,
+                       const void *rho, const void *eta, const void *hfilm, const void *normal,
+                       const void *out, const double *gravity, double dt, void *stream) {
+  if (!ctx) return MAFP_EINVAL;
+  int rc;
+  if ((rc = check_dtype(ctx, dtype))) return rc;
+  if (n < 0) return fail(ctx, MAFP_EINVAL, "negative particle count");
+  if (n == 0) return MAFP_OK;
+  REQUIRE(model); REQUIRE(vp); REQUIRE(rho); REQUIRE(eta); REQUIRE(hfilm); REQUIRE(normal);
+  REQUIRE(out); REQUIRE(gravity);
+  if (!(dt >= 0.0)) return fail(ctx, MAFP_EINVAL, "dt must be >= 0");
+  if (ensure_device(ctx)) return MAFP_ECUDA;
+  return film_momentum(ctx, n, dtype, model, vp, rho, eta, hfilm, normal, out, gravity, dt,
+                       (cudaStream_t)stream);
+}
+
+int mafp_plane_flux(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_old,
+                    const void *pos_new, const void *mass, const void *rho, const double *point,
+                    const double *normal, double *acc_dev, void *stream) {
+  if (!ctx) return MAFP_EINVAL;
+  int rc;
+  if ((rc = check_dtype(ctx, dtype))) return rc;
+  if (n < 0) return fail(ctx, MAFP_EINVAL, "negative particle count");
+  if (n == 0) return MAFP_OK;
+  REQUIRE(pos_old); REQUIRE(pos_new); REQUIRE(mass); REQUIRE(rho); REQUIRE(point);
+  REQUIRE(normal); REQUIRE(acc_dev);
+  if (ensure_device(ctx)) return MAFP_ECUDA;
+  return plane_flux(ctx, n, dtype, pos_old, pos_new, mass, rho, point, normal, acc_dev,
+                    (cudaStream_t)stream);
+}
+
+int mafp_normal_stress(mafp_ctx *ctx, int64_t n, int32_t dtype, const uint8_t *select,
+                       const void *out, const void *eta, const void *normal, double *acc_dev,
+                       void *stream) {
+  if (!ctx) return MAFP_EINVAL;
+  int rc;
+  if ((rc = check_dtype(ctx, dtype))) return rc;
+  if (n < 0) return fail(ctx, MAFP_EINVAL, "negative particle count");
+  if (n == 0) return MAFP_OK;
+  REQUIRE(select); REQUIRE(out); REQUIRE(eta); REQUIRE(normal); REQUIRE(acc_dev);
+  if (ensure_device(ctx)) return MAFP_ECUDA;
+  return normal_stress(ctx, n, dtype, select, out, eta, normal, acc_dev, (cudaStream_t)stream);
 }
 
 int mafp_ghost_sources(mafp_ctx *ctx, int64_t n, const uint8_t *model, const int64_t *row_ptr,

@@ -90,6 +90,9 @@ def lib():
         L.mafp_ghost_sources.argtypes = [p, i64, p, p, p, p, p]
         L.mafp_ghost_seed.argtypes = [p, i64, i32, p, p, p, i64, p, p, p, p]
         L.mafp_ghost_append.argtypes = [p, i64, i64, i32, p, p, i64, p, p]
+        L.mafp_film_momentum.argtypes = [p, i64, i32, p, p, p, p, p, p, p, p, C.c_double, p]
+        L.mafp_plane_flux.argtypes = [p, i64, i32, p, p, p, p, p, p, p, p]
+        L.mafp_normal_stress.argtypes = [p, i64, i32, p, p, p, p, p, p]
         L.mafp_classify_pca.argtypes = [p, i64, i32] + [p] * 17
         L.mafp_build_stencils.argtypes = [p, i64, i32, p, p, p, p, p, p, p, p, p]
         L.mafp_apply_ops.argtypes = [p, i64, i32, p, p, p, p, p, p]
@@ -106,7 +109,8 @@ def lib():
                      "mafp_classify_pca", "mafp_build_stencils",
                      "mafp_apply_ops", "mafp_transpose_map", "mafp_apply_ops_backward",
                      "mafp_build_stencils_backward", "mafp_remap_switched",
-                     "mafp_ghost_sources", "mafp_ghost_seed", "mafp_ghost_append"):
+                     "mafp_ghost_sources", "mafp_ghost_seed", "mafp_ghost_append",
+                     "mafp_film_momentum", "mafp_plane_flux", "mafp_normal_stress"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -435,3 +439,52 @@ def ghost_append(ctx: Context, n_regular: int, n_ghost: int, ghost: dict, all_: 
     ctx.check(lib().mafp_ghost_append(ctx.handle, int(n_regular), int(n_ghost), dtype,
                                       C.byref(sg), C.byref(sa), int(cap_all), _ptr(n_all),
                                       _stream(stream)))
+
+
+def _d3(v):
+    a = (C.c_double * 3)(*[float(x) for x in v])
+    return a
+
+
+def film_momentum(ctx: Context, model, vp, rho, eta, hfilm, normal, out, gravity, dt: float,
+                  dtype=F32_REFINED, stream=None):
+    """Eq. FilmMomentum, explicit step for the film particles (vp updated in place)."""
+    n = model.numel()
+    rd = real_dtype(dtype)
+    _need(model, "model", torch.uint8, n)
+    for t, nm, k in ((vp, "vp", 4), (normal, "normal", 4), (out, "out", 16)):
+        _need(t, nm, rd, k * n)
+    for t, nm in ((rho, "rho"), (eta, "eta"), (hfilm, "hfilm")):
+        _need(t, nm, rd, n)
+    g = _d3(gravity)
+    ctx.check(lib().mafp_film_momentum(ctx.handle, n, dtype, _ptr(model), _ptr(vp), _ptr(rho),
+                                       _ptr(eta), _ptr(hfilm), _ptr(normal), _ptr(out), g,
+                                       float(dt), _stream(stream)))
+
+
+def plane_flux(ctx: Context, pos_old, pos_new, mass, rho, point, normal, acc,
+               dtype=F32_REFINED, stream=None):
+    """Volume through a plane over one step, accumulated into acc[0:2] (float64, device)."""
+    n = pos_old.shape[0]
+    rd = real_dtype(dtype)
+    _need(pos_old, "pos_old", rd, 4 * n)
+    _need(pos_new, "pos_new", rd, 4 * n)
+    _need(mass, "mass", rd, n)
+    _need(rho, "rho", rd, n)
+    _need(acc, "acc", torch.float64, 2)
+    ctx.check(lib().mafp_plane_flux(ctx.handle, n, dtype, _ptr(pos_old), _ptr(pos_new),
+                                    _ptr(mass), _ptr(rho), _d3(point), _d3(normal), _ptr(acc),
+                                    _stream(stream)))
+
+
+def normal_stress(ctx: Context, select, out, eta, normal, acc, dtype=F32_REFINED, stream=None):
+    """Sum and count of n^T S n over the selected particles into acc[0:2] (float64, device)."""
+    n = select.numel()
+    rd = real_dtype(dtype)
+    _need(select, "select", torch.uint8, n)
+    _need(out, "out", rd, 16 * n)
+    _need(eta, "eta", rd, n)
+    _need(normal, "normal", rd, 4 * n)
+    _need(acc, "acc", torch.float64, 2)
+    ctx.check(lib().mafp_normal_stress(ctx.handle, n, dtype, _ptr(select), _ptr(out), _ptr(eta),
+                                       _ptr(normal), _ptr(acc), _stream(stream)))
