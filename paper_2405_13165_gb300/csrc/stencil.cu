@@ -14,17 +14,27 @@ namespace mafp {
 
 __global__ void k_reset_queue(DevStatus *st) { st->fallback_count = 0; }
 
+// Per-lane cache of (q, w) for the refinement and coefficient passes (FP32
+// path): 176 entries per 3D row, 48 per film row; entries beyond it are
+// gathered and recomputed as in the first pass.
+template <typename C, int M, int G>
+struct StCache {
+  static constexpr int KC = sizeof(C) == 4 ? (M == 10 ? 176 : 48) / G : 0;
+  static constexpr int BYTES = (kStThreads / G) * KC * G * (int)sizeof(float4);
+  static constexpr int SMEM = BYTES + (kStThreads / G) * StSmem<M, G>::PER_GROUP * (int)sizeof(C);
+};
+
 constexpr int kGatherU = 2;   // neighbours a lane gathers ahead of use
 constexpr int kGatherR = 2;   // the same in the refinement pass (more live registers)
 
 // Process particle i with a group of G lanes.  Returns (through *result)
 //  0 = written, 1 = deficient (zeros written), 2 = queued for FP64.
-template <typename TS, typename C, int M, int G, bool REFINE, bool QUEUE>
+template <typename TS, typename C, int M, int G, bool REFINE, bool QUEUE, int KC = 0>
 __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *model,
                                  const vec4_t<TS> *frame, const long long *row_ptr,
                                  const int32_t *col, vec4_t<TS> *coef, const StParams<C> &sp,
                                  C *sm /* per-group scratch, >= pad_to(NR*M or NA, G) */,
-                                 int *result, float *cond_out) {
+                                 int *result, float *cond_out, float4 *qw = nullptr) {
   constexpr int NA = Basis<M>::NA, NR = Basis<M>::NR;
   constexpr int VA = pad_to(NA, G), VR = pad_to(NR * M, G);
   using V = vec4_t<TS>;
@@ -48,7 +58,8 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
 #pragma unroll
   for (int k = 0; k < VA; ++k) A[k] = C(0);
   int cnt = 0;
-  for (long long e0 = b + lane; e0 < e1; e0 += kGatherU * G) {
+  int kk = 0;   // this lane's running entry index: entry b + lane + kk G
+  for (long long e0 = b + lane; e0 < e1; e0 += kGatherU * G, kk += kGatherU) {
     V xs[kGatherU];
     bool oks[kGatherU];
     gather_row<kGatherU, G>(e0, e1, i, mi, col, pos, model, xs, oks);
@@ -58,6 +69,10 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
       C w = basis_at<M, C>(xi, xs[u], hinv, t1, t2, sp, p);
       w = oks[u] ? w : C(0);   // other model / past the row end: contributes exact zeros
       cnt += oks[u] ? 1 : 0;
+      if constexpr (KC > 0) {
+        // keep (q, w) for the later passes: they rebuild p without a gather
+        if (kk + u < KC) qw[(kk + u) * G + lane] = make_float4(p[1], p[2], M == 10 ? p[3] : 0.f, w);
+      }
 #pragma unroll
       for (int r = 0; r < M; ++r) {
         const C wp = w * p[r];
@@ -99,6 +114,9 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
     *cond_out = INFINITY;
     return;
   }
+  // entries of this lane, and how many of them the cache holds
+  const int nloc = e1 > b + lane ? (int)((e1 - b - lane + G - 1) / G) : 0;
+  const int ncache = KC > 0 ? min(nloc, KC) : 0;
   // ---- solve
   C lam[NR][M];
 #pragma unroll
@@ -113,7 +131,22 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
     C R[VR];
 #pragma unroll
     for (int k = 0; k < VR; ++k) R[k] = C(0);
-    for (long long e0 = b + lane; e0 < e1; e0 += kGatherR * G) {
+    for (int q = 0; q < ncache; ++q) {
+      const float4 c4 = qw[q * G + lane];
+      C p[M];
+      basis_from_q<M, C>(c4, p);
+      const C w = c4.w;
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        C s = 0;
+#pragma unroll
+        for (int r = 0; r < M; ++r) s += p[r] * lam[k][r];
+        const C c = w * s;
+#pragma unroll
+        for (int r = 0; r < M; ++r) R[k * M + r] += c * p[r];
+      }
+    }
+    for (long long e0 = b + lane + (long long)ncache * G; e0 < e1; e0 += kGatherR * G) {
       V xs[kGatherR];
       bool oks[kGatherR];
       gather_row<kGatherR, G>(e0, e1, i, mi, col, pos, model, xs, oks);
@@ -150,7 +183,34 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
   }
   // ---- coefficients
   const C h2inv = hinv * hinv;
-  for (long long e0 = b + lane; e0 < e1; e0 += kGatherU * G) {
+  auto write_coef = [&](long long e, const C (&p)[M], C w) {
+    C c[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      C s = 0;
+#pragma unroll
+      for (int r = 0; r < M; ++r) s += p[r] * lam[k][r];
+      c[k] = w * s;
+    }
+    vec4_t<TS> out;
+    if constexpr (M == 10) {
+      out = mk4<TS>(TS(c[0] * hinv), TS(c[1] * hinv), TS(c[2] * hinv), TS(c[3] * h2inv));
+    } else {
+      const C gx = (c[0] * t1[0] + c[1] * t2[0]) * hinv;
+      const C gy = (c[0] * t1[1] + c[1] * t2[1]) * hinv;
+      const C gz = (c[0] * t1[2] + c[1] * t2[2]) * hinv;
+      out = mk4<TS>(TS(gx), TS(gy), TS(gz), TS(c[2] * h2inv));
+    }
+    st4(coef + e, out);
+  };
+  for (int q = 0; q < ncache; ++q) {
+    const float4 c4 = qw[q * G + lane];
+    C p[M];
+    basis_from_q<M, C>(c4, p);
+    if (c4.w != 0.f) write_coef(b + lane + (long long)q * G, p, C(c4.w));
+    else st4(coef + b + lane + (long long)q * G, mk4<TS>(0, 0, 0, 0));
+  }
+  for (long long e0 = b + lane + (long long)ncache * G; e0 < e1; e0 += kGatherU * G) {
     V xs[kGatherU];
     bool oks[kGatherU];
     gather_row<kGatherU, G>(e0, e1, i, mi, col, pos, model, xs, oks);
@@ -194,9 +254,13 @@ __global__ void __launch_bounds__(kStThreads, M == 10 ? 4 : 6) k_stencil(
     float *cond, StParams<C> sp, DevStatus *st, int32_t *queue) {
   constexpr int NA = Basis<M>::NA, NR = Basis<M>::NR;
   constexpr int SMG = StSmem<M, G>::PER_GROUP;
-  __shared__ C smem[(kStThreads / G) * SMG];
+  constexpr int KC = StCache<C, M, G>::KC;
+  extern __shared__ __align__(16) unsigned char st_smem[];
+  float4 *qcache = reinterpret_cast<float4 *>(st_smem);
+  C *smem = reinterpret_cast<C *>(st_smem + StCache<C, M, G>::BYTES);
   const int grp = threadIdx.x / G;
   C *sm = smem + grp * SMG;
+  float4 *qw = qcache + grp * KC * G;
   const int lane = threadIdx.x & (G - 1);
   const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
@@ -205,8 +269,8 @@ __global__ void __launch_bounds__(kStThreads, M == 10 ? 4 : 6) k_stencil(
     if (model[i] != want) continue;   // uniform within the group
     int res;
     float cd = 0.0f;
-    stencil_particle<TS, C, M, G, REFINE, QUEUE>(i, pos, model, frame, row_ptr, col, coef, sp,
-                                                 sm, &res, &cd);
+    stencil_particle<TS, C, M, G, REFINE, QUEUE, KC>(i, pos, model, frame, row_ptr, col, coef,
+                                                     sp, sm, &res, &cd, qw);
     if (lane == 0) {
       if (res == 2) {
         const int slot = atomicAdd(&st->fallback_count, 1);
@@ -263,8 +327,15 @@ static void launch_stencil(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void 
   snprintf(name, sizeof(name), "k_stencil<%s,M=%d,G=%d,%s>", sizeof(TS) == 4 ? "f32" : "f64",
            M, G, REFINE ? "refined" : "plain");
   const int blocks = grid_for(n * G, kStThreads, sm_count() * 64);
+  constexpr int smem = StCache<C, M, G>::SMEM;
+  static bool attr_set = false;
+  if (!attr_set && smem > 48 * 1024) {
+    cudaFuncSetAttribute(k_stencil<TS, C, M, G, REFINE, QUEUE>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr_set = true;
+  }
   MAFP_TIMED(ctx, s, name,
-             k_stencil<TS, C, M, G, REFINE, QUEUE><<<blocks, kStThreads, 0, s>>>(
+             k_stencil<TS, C, M, G, REFINE, QUEUE><<<blocks, kStThreads, smem, s>>>(
                  n, (const V *)pos_h, model, (const V *)frame, rp, col, (V *)coef, status, cond,
                  sp, ctx->d_status, ctx->fallback));
 }

@@ -55,6 +55,22 @@ __device__ __forceinline__ C basis_at(const V &xi, const V &xj, C hinv, const C 
   return w;
 }
 
+// The same monomials rebuilt from a cached (q, w): q = (x_j - x_i) / h_i in 3D,
+// (xi, eta) in 2D, with the products taken exactly as basis_at takes them.
+template <int M, typename C>
+__device__ __forceinline__ void basis_from_q(const float4 &c, C (&p)[M]) {
+  if constexpr (M == 10) {
+    const C qx = c.x, qy = c.y, qz = c.z;
+    p[0] = C(1); p[1] = qx; p[2] = qy; p[3] = qz;
+    p[4] = qx * qx; p[5] = qy * qy; p[6] = qz * qz;
+    p[7] = qx * qy; p[8] = qx * qz; p[9] = qy * qz;
+  } else {
+    const C xi_ = c.x, et_ = c.y;
+    p[0] = C(1); p[1] = xi_; p[2] = et_;
+    p[3] = xi_ * xi_; p[4] = xi_ * et_; p[5] = et_ * et_;
+  }
+}
+
 // Right-hand side k (unscaled: the 1/h and 1/h^2 factors are applied to the output).
 template <int M, typename C>
 __device__ __forceinline__ C rhs(int k, int r) {
