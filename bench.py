@@ -82,7 +82,8 @@ def parse():
                          "cube-on-sheet clouds, forward pass replayed from a CUDA graph; "
                          "tray: the 16M-particle 20-step loop with model transitions")
     ap.add_argument("--tuning", default=None,
-                    help="fixed launch shapes 'g3d,g2d,gapply' instead of the autotuner")
+                    help="fixed launch shapes 'g3d,g2d,gapply[,ggrad3d]' instead of the autotuner "
+                         "(ggrad3d defaults to the library's 4)")
     return ap.parse_args()
 
 
@@ -273,8 +274,9 @@ def bench_gpu(args):
 
     from paper_2405_13165_gb300 import autotune
     if args.tuning:
-        g3, g2, ga = (int(v) for v in args.tuning.split(","))
-        ctx.set_tuning(stencil3d_group=g3, stencil2d_group=g2, apply_group=ga)
+        g = [int(v) for v in args.tuning.split(",")]
+        ctx.set_tuning(stencil3d_group=g[0], stencil2d_group=g[1], apply_group=g[2],
+                       grad3d_group=g[3] if len(g) > 3 else 4)
         tuned = {"tuning": ctx.tuning(), "source": "command line"}
     else:
         tuned = autotune.tune(ctx, pipe, d, use_cache=False)

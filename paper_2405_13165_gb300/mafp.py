@@ -48,7 +48,7 @@ class Status(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("stencil3d_group", C.c_int32), ("stencil2d_group", C.c_int32),
-                ("apply_group", C.c_int32), ("reserved", C.c_int32)]
+                ("apply_group", C.c_int32), ("grad3d_group", C.c_int32)]
 
 
 class KernelTime(C.Structure):
@@ -192,7 +192,7 @@ class Context:
     def tuning(self) -> dict:
         t = Tuning()
         self.check(lib().mafp_get_tuning(self.handle, C.byref(t)))
-        return {k: getattr(t, k) for k, _ in Tuning._fields_ if k != "reserved"}
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
     def set_tuning(self, **kw):
         cur = self.tuning()

@@ -81,3 +81,33 @@ def test_gradcheck_fp64_tiny_cloud():
     assert torch.autograd.gradcheck(f, (xyz, fields), eps=1e-7, atol=1e-6, rtol=1e-5,
                                     nondet_tol=1e-9, fast_mode=True)
     ctx.close()
+
+
+@pytest.mark.parametrize("dtype", [M.F32_REFINED, M.F64])
+def test_adjoint_launch_shapes_agree_with_oracle(dtype):
+    """Every grad3d_group (lanes per 3D particle of the position adjoint) gives
+    the oracle's gradient; in FP64 the 4-lane choice runs the 8-lane kernel."""
+    c = C.cube_on_sheet(0.04, cube=0.32, sheet=1.0)
+    ctx, d, rp, col, frame = _setup(c, dtype)
+    rng = np.random.default_rng(11)
+    Gr = rng.normal(size=(c.n, 4, 4))
+    P = c.pos_h.astype(np.float64)
+    orp, ocol = O.neighbours(P)
+    og = O.stencil_grad(P, c.model, orp, ocol, c.vp, Gr)
+    scale = np.abs(og[:, :3]).max(0)
+    tol = 2e-3 if dtype != M.F64 else 1e-8
+    gout = torch.tensor(Gr, dtype=d["pos_h"].dtype, device="cuda").contiguous()
+    gpos = torch.empty_like(d["pos_h"])
+    for gb in (4, 8, 16, 32):
+        ctx.set_tuning(grad3d_group=gb)
+        assert ctx.tuning()["grad3d_group"] == gb
+        gpos.fill_(float("nan"))
+        M.build_stencils_backward(ctx, d["pos_h"], d["model"], frame, rp, col, d["fields"],
+                                  gout, gpos, dtype)
+        got = gpos.double().cpu().numpy()
+        err = np.abs(got[:, :3] - og[:, :3]).max(0)
+        assert np.all(err <= tol * scale), (gb, err / scale)
+        assert np.all(got[:, 3] == 0)
+    with pytest.raises(M.MafpError):
+        ctx.set_tuning(grad3d_group=2)
+    ctx.close()
