@@ -53,10 +53,11 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
     t2[2] = n0 * t1[1] - n1 * t1[0];
   }
   const long long b = row_ptr[i], e1 = row_ptr[i + 1];
-  // ---- moments
-  C A[VA];
+  // ---- moments (the distinct ones)
+  constexpr int VM = pad_to(Moments<M>::N, G);
+  C A[VM];
 #pragma unroll
-  for (int k = 0; k < VA; ++k) A[k] = C(0);
+  for (int k = 0; k < VM; ++k) A[k] = C(0);
   int cnt = 0;
   int kk = 0;   // this lane's running entry index: entry b + lane + kk G
   for (long long e0 = b + lane; e0 < e1; e0 += kGatherU * G, kk += kGatherU) {
@@ -73,23 +74,19 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
         // keep (q, w) for the later passes: they rebuild p without a gather
         if (kk + u < KC) qw[(kk + u) * G + lane] = make_float4(p[1], p[2], M == 10 ? p[3] : 0.f, w);
       }
-#pragma unroll
-      for (int r = 0; r < M; ++r) {
-        const C wp = w * p[r];
-#pragma unroll
-        for (int c = 0; c <= r; ++c) A[pk(r, c)] += wp * p[c];
-      }
+      add_moments<M, C, VM>(A, w, p);
     }
   }
   cnt = group_sum<G>(cnt);
-  reduce_scatter<G, VA>(A);
+  reduce_scatter<G, VM>(A);
   __syncwarp(gm);
 #pragma unroll
-  for (int k = 0; k < VA / G; ++k) sm[lane * (VA / G) + k] = A[k];
+  for (int k = 0; k < VM / G; ++k) sm[lane * (VM / G) + k] = A[k];
   __syncwarp(gm);
   C L[NA];
+  constexpr MomentTable<M> MT = Moments<M>::T;
 #pragma unroll
-  for (int k = 0; k < NA; ++k) L[k] = sm[k];
+  for (int k = 0; k < NA; ++k) L[k] = sm[MT.idx[k]];
   __syncwarp(gm);
   C tr = 0;
 #pragma unroll

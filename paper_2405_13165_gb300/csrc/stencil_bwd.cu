@@ -86,12 +86,18 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
   };
   // ---- one pass: moments A = sum_j w_j p_j p_j^T and lbar_k = sum_j gbar_jk w_j p_j
   // (gbar depends on the fields only, so it needs no solution yet)
-  C A[VA];
+  constexpr int VM = pad_to(Moments<M>::N, G);
+  C A[VM];   // the distinct moments
 #pragma unroll
-  for (int k = 0; k < VA; ++k) A[k] = C(0);
+  for (int k = 0; k < VM; ++k) A[k] = C(0);
   C R[VR];
 #pragma unroll
   for (int k = 0; k < VR; ++k) R[k] = C(0);
+  // lbar is linear in the field differences: the pass sums B_f = sum_j w_j
+  // du_jf p_j and lbar_k = sum_f gout[i][f][k] B_f (scaled as gbar) follows
+  C Bf[4 * M];
+#pragma unroll
+  for (int k = 0; k < 4 * M; ++k) Bf[k] = C(0);
   int cnt = 0;
   for (long long e0 = b + lane; e0 < e1; e0 += kGradGatherA * G) {
     V xs[kGradGatherA], fs[kGradGatherA];
@@ -100,35 +106,52 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
     gather_row_f<kGradGatherA, G>(e0, e1, i, mi, col, pos, model, fields, xs, fs, js, oks);
 #pragma unroll
     for (int u = 0; u < kGradGatherA; ++u) {
-      C p[M], gb[NR];
+      C p[M];
       C w = basis_at<M, C>(xi, xs[u], hinv, t1, t2, sp, p);
       w = oks[u] ? w : C(0);   // other model / past the row end: contributes exact zeros
       cnt += oks[u] ? 1 : 0;
+      add_moments<M, C, VM>(A, w, p);
+      const V fj = fs[u];
+      const C wdu[4] = {w * (C(fj.x) - C(fi.x)), w * (C(fj.y) - C(fi.y)),
+                        w * (C(fj.z) - C(fi.z)), w * (C(fj.w) - C(fi.w))};
 #pragma unroll
-      for (int r = 0; r < M; ++r) {
-        const C wp = w * p[r];
+      for (int f = 0; f < 4; ++f)
 #pragma unroll
-        for (int c = 0; c <= r; ++c) A[pk(r, c)] += wp * p[c];
-      }
-      gbar(fs[u], gb);
+        for (int r = 0; r < M; ++r) Bf[f * M + r] += wdu[f] * p[r];
+    }
+  }
 #pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        const C gw = gb[k] * w;
+  for (int r = 0; r < M; ++r) {
+    C g4[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int r = 0; r < M; ++r) R[k * M + r] += gw * p[r];
-      }
+    for (int f = 0; f < 4; ++f) {
+      g4[0] += C(go[f].x) * Bf[f * M + r];
+      g4[1] += C(go[f].y) * Bf[f * M + r];
+      g4[2] += C(go[f].z) * Bf[f * M + r];
+      g4[3] += C(go[f].w) * Bf[f * M + r];
+    }
+    if constexpr (M == 10) {
+      R[0 * M + r] = g4[0] * hinv;
+      R[1 * M + r] = g4[1] * hinv;
+      R[2 * M + r] = g4[2] * hinv;
+      R[3 * M + r] = g4[3] * h2inv;
+    } else {
+      R[0 * M + r] = (g4[0] * t1[0] + g4[1] * t1[1] + g4[2] * t1[2]) * hinv;
+      R[1 * M + r] = (g4[0] * t2[0] + g4[1] * t2[1] + g4[2] * t2[2]) * hinv;
+      R[2 * M + r] = g4[3] * h2inv;
     }
   }
   cnt = group_sum<G>(cnt);
-  reduce_scatter<G, VA>(A);
+  reduce_scatter<G, VM>(A);
   reduce_scatter<G, VR>(R);
   __syncwarp(gm);
 #pragma unroll
-  for (int k = 0; k < VA / G; ++k) sm[lane * (VA / G) + k] = A[k];
+  for (int k = 0; k < VM / G; ++k) sm[lane * (VM / G) + k] = A[k];
   __syncwarp(gm);
   C L[NA];
+  constexpr MomentTable<M> MT = Moments<M>::T;
 #pragma unroll
-  for (int k = 0; k < NA; ++k) L[k] = sm[k];
+  for (int k = 0; k < NA; ++k) L[k] = sm[MT.idx[k]];
   __syncwarp(gm);
 #pragma unroll
   for (int k = 0; k < VR / G; ++k) sm[lane * (VR / G) + k] = R[k];
@@ -183,7 +206,8 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
     const C dx = C(xj.x) - C(xi.x), dy = C(xj.y) - C(xi.y), dz = C(xj.z) - C(xi.z);
     const C s2 = ((dx * dx + dy * dy) + dz * dz) * (hinv * hinv);
     const C dws = s2 <= C(1) ? a2 * exp(-sp.alpha * s2) : C(0);
-    // pbar = w sum_k ((gbar_k - t_k) lambda_k - s_k mu_k), the factor w applied last
+    // pbar = w sum_k ((gbar_k - t_k) lambda_k - s_k mu_k); pbar_0 is not needed
+    // (d p_0 / d q = 0) and the factor w is applied to the gradient below
     C wbar = 0, pbar[M];
 #pragma unroll
     for (int r = 0; r < M; ++r) pbar[r] = 0;
@@ -198,24 +222,22 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
       const C a = gb[k] - t;
       wbar += a * s;
 #pragma unroll
-      for (int r = 0; r < M; ++r) pbar[r] += a * lam[k][r] - s * mu[k][r];
+      for (int r = 1; r < M; ++r) pbar[r] += a * lam[k][r] - s * mu[k][r];
     }
-#pragma unroll
-    for (int r = 0; r < M; ++r) pbar[r] *= w;
     const C wq = dws * wbar;
     C d[3];
     if constexpr (M == 10) {
       const C qx = dx * hinv, qy = dy * hinv, qz = dz * hinv;
-      const C gx = pbar[1] + C(2) * qx * pbar[4] + qy * pbar[7] + qz * pbar[8];
-      const C gy = pbar[2] + C(2) * qy * pbar[5] + qx * pbar[7] + qz * pbar[9];
-      const C gz = pbar[3] + C(2) * qz * pbar[6] + qx * pbar[8] + qy * pbar[9];
+      const C gx = w * (pbar[1] + C(2) * qx * pbar[4] + qy * pbar[7] + qz * pbar[8]);
+      const C gy = w * (pbar[2] + C(2) * qy * pbar[5] + qx * pbar[7] + qz * pbar[9]);
+      const C gz = w * (pbar[3] + C(2) * qz * pbar[6] + qx * pbar[8] + qy * pbar[9]);
       d[0] = (gx + wq * qx) * hinv;
       d[1] = (gy + wq * qy) * hinv;
       d[2] = (gz + wq * qz) * hinv;
     } else {
       const C xi_ = p[1], et_ = p[2];
-      const C xb = pbar[1] + C(2) * xi_ * pbar[3] + et_ * pbar[4];
-      const C eb = pbar[2] + xi_ * pbar[4] + C(2) * et_ * pbar[5];
+      const C xb = w * (pbar[1] + C(2) * xi_ * pbar[3] + et_ * pbar[4]);
+      const C eb = w * (pbar[2] + xi_ * pbar[4] + C(2) * et_ * pbar[5]);
       d[0] = (xb * t1[0] + eb * t2[0]) * hinv + wq * dx * hinv * hinv;
       d[1] = (xb * t1[1] + eb * t2[1]) * hinv + wq * dy * hinv * hinv;
       d[2] = (xb * t1[2] + eb * t2[2]) * hinv + wq * dz * hinv * hinv;

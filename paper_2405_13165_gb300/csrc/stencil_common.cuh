@@ -22,6 +22,63 @@ template <> struct Basis<6> {
 __host__ __device__ constexpr int pad_to(int v, int g) { return ((v + g - 1) / g) * g; }
 __host__ __device__ constexpr int pk(int r, int c) { return r * (r + 1) / 2 + c; }
 
+// Distinct moments of the basis products.  Every entry A_rc = sum_j w_j p_r p_c
+// is the weighted moment of the monomial p_r p_c (degree <= 4); equal
+// monomials give equal entries, so only the distinct ones are summed: 35 of
+// the 55 entries in 3D, 15 of the 21 in 2D.  Moment m is accumulated as
+// (w p_rep_r[m]) p_rep_c[m]; entry pk(r, c) reads moment idx[pk(r, c)].
+template <int M>
+struct MomentTable {
+  int n = 0;
+  int rep_r[Basis<M>::NA] = {};
+  int rep_c[Basis<M>::NA] = {};
+  int idx[Basis<M>::NA] = {};
+};
+// Exponents of the basis monomials: (1, qx, qy, qz, qx^2, qy^2, qz^2, qx qy,
+// qx qz, qy qz) in 3D, (1, xi, eta, xi^2, xi eta, eta^2) in 2D.
+template <int M>
+constexpr MomentTable<M> make_moment_table() {
+  int e[10][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                  {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+  if (M == 6) {
+    const int e2[6][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {2, 0, 0}, {1, 1, 0}, {0, 2, 0}};
+    for (int r = 0; r < 6; ++r)
+      for (int a = 0; a < 3; ++a) e[r][a] = e2[r][a];
+  }
+  MomentTable<M> t;
+  int sum[Basis<M>::NA][3] = {};
+  for (int r = 0; r < M; ++r)
+    for (int c = 0; c <= r; ++c) {
+      const int s0 = e[r][0] + e[c][0], s1 = e[r][1] + e[c][1], s2 = e[r][2] + e[c][2];
+      int m = 0;
+      while (m < t.n && !(sum[m][0] == s0 && sum[m][1] == s1 && sum[m][2] == s2)) ++m;
+      if (m == t.n) {
+        sum[m][0] = s0;
+        sum[m][1] = s1;
+        sum[m][2] = s2;
+        t.rep_r[m] = r;
+        t.rep_c[m] = c;
+        ++t.n;
+      }
+      t.idx[r * (r + 1) / 2 + c] = m;
+    }
+  return t;
+}
+template <int M>
+struct Moments {
+  static constexpr MomentTable<M> T = make_moment_table<M>();
+  static constexpr int N = T.n;
+};
+static_assert(Moments<10>::N == 35 && Moments<6>::N == 15, "distinct moments of degree <= 4");
+
+// Add w p p^T of one neighbour to the distinct moments.
+template <int M, typename C, int VM>
+__device__ __forceinline__ void add_moments(C (&mom)[VM], C w, const C (&p)[M]) {
+  constexpr MomentTable<M> T = Moments<M>::T;
+#pragma unroll
+  for (int m = 0; m < Moments<M>::N; ++m) mom[m] += (w * p[T.rep_r[m]]) * p[T.rep_c[m]];
+}
+
 template <typename C>
 struct StParams {
   C alpha, ea, inv_den;   // W(s) = (exp(-alpha s^2) - ea) * inv_den, s <= 1
