@@ -24,7 +24,9 @@ struct StCache {
   static constexpr int SMEM = BYTES + (kStThreads / G) * StSmem<M, G>::PER_GROUP * (int)sizeof(C);
 };
 
-constexpr int kGatherU = 2;   // neighbours a lane gathers ahead of use
+// neighbours a lane gathers ahead of use: 4 for 3D rows (long rows, the loads
+// in flight together), 2 for film rows
+template <int M> constexpr int kGatherU = M == 10 ? 4 : 2;
 constexpr int kGatherR = 2;   // the same in the refinement pass (more live registers)
 
 // Process particle i with a group of G lanes.  Returns (through *result)
@@ -60,12 +62,12 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
   for (int k = 0; k < VM; ++k) A[k] = C(0);
   int cnt = 0;
   int kk = 0;   // this lane's running entry index: entry b + lane + kk G
-  for (long long e0 = b + lane; e0 < e1; e0 += kGatherU * G, kk += kGatherU) {
-    V xs[kGatherU];
-    bool oks[kGatherU];
-    gather_row<kGatherU, G>(e0, e1, i, mi, col, pos, model, xs, oks);
+  for (long long e0 = b + lane; e0 < e1; e0 += kGatherU<M> * G, kk += kGatherU<M>) {
+    V xs[kGatherU<M>];
+    bool oks[kGatherU<M>];
+    gather_row<kGatherU<M>, G>(e0, e1, i, mi, col, pos, model, xs, oks);
 #pragma unroll
-    for (int u = 0; u < kGatherU; ++u) {
+    for (int u = 0; u < kGatherU<M>; ++u) {
       C p[M];
       C w = basis_at<M, C>(xi, xs[u], hinv, t1, t2, sp, p);
       w = oks[u] ? w : C(0);   // other model / past the row end: contributes exact zeros
@@ -207,12 +209,12 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
     if (c4.w != 0.f) write_coef(b + lane + (long long)q * G, p, C(c4.w));
     else st4(coef + b + lane + (long long)q * G, mk4<TS>(0, 0, 0, 0));
   }
-  for (long long e0 = b + lane + (long long)ncache * G; e0 < e1; e0 += kGatherU * G) {
-    V xs[kGatherU];
-    bool oks[kGatherU];
-    gather_row<kGatherU, G>(e0, e1, i, mi, col, pos, model, xs, oks);
+  for (long long e0 = b + lane + (long long)ncache * G; e0 < e1; e0 += kGatherU<M> * G) {
+    V xs[kGatherU<M>];
+    bool oks[kGatherU<M>];
+    gather_row<kGatherU<M>, G>(e0, e1, i, mi, col, pos, model, xs, oks);
 #pragma unroll
-    for (int u = 0; u < kGatherU; ++u) {
+    for (int u = 0; u < kGatherU<M>; ++u) {
     const long long e = e0 + (long long)u * G;
     if (e >= e1) break;
     vec4_t<TS> out = mk4<TS>(0, 0, 0, 0);
@@ -245,7 +247,7 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
 
 // Main kernel: every particle of model (M == 10 ? 3D : 2D).
 template <typename TS, typename C, int M, int G, bool REFINE, bool QUEUE>
-__global__ void __launch_bounds__(kStThreads, M == 10 ? 4 : 6) k_stencil(
+__global__ void __launch_bounds__(kStThreads, sizeof(C) == 4 ? (M == 10 ? 4 : 6) : 1) k_stencil(
     int64_t n, const vec4_t<TS> *pos, const uint8_t *model, const vec4_t<TS> *frame,
     const long long *row_ptr, const int32_t *col, vec4_t<TS> *coef, uint8_t *status,
     float *cond, StParams<C> sp, DevStatus *st, int32_t *queue) {
