@@ -28,14 +28,15 @@ __global__ void __launch_bounds__(kApThreads) k_apply(int64_t n, const long long
     T acc[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = T(0);
-    long long e = b + lane;
-    for (; e + (U - 1) * G < e1; e += U * G) {
+    // U entries per lane in flight; past the row end the slot reads particle
+    // i itself with a zero coefficient (an exact zero contribution)
+    for (long long e = b + lane; e < e1; e += U * G) {
       int j[U];
       V c[U], f[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) j[u] = __ldg(col + e + u * G);
+      for (int u = 0; u < U; ++u) j[u] = e + u * G < e1 ? __ldg(col + e + u * G) : (int)i;
 #pragma unroll
-      for (int u = 0; u < U; ++u) c[u] = ld4(coef + e + u * G);
+      for (int u = 0; u < U; ++u) c[u] = e + u * G < e1 ? ld4(coef + e + u * G) : mk4<T>(0, 0, 0, 0);
 #pragma unroll
       for (int u = 0; u < U; ++u) f[u] = ld4(fields + j[u]);
 #pragma unroll
@@ -48,19 +49,6 @@ __global__ void __launch_bounds__(kApThreads) k_apply(int64_t n, const long long
           acc[4 * q + 2] += c[u].z * fv[q];
           acc[4 * q + 3] += c[u].w * fv[q];
         }
-      }
-    }
-    for (; e < e1; e += G) {
-      const int j = __ldg(col + e);
-      const V c = ld4(coef + e);
-      const V f = ld4(fields + j);
-      const T fv[4] = {f.x - fi.x, f.y - fi.y, f.z - fi.z, f.w - fi.w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc[4 * q + 0] += c.x * fv[q];
-        acc[4 * q + 1] += c.y * fv[q];
-        acc[4 * q + 2] += c.z * fv[q];
-        acc[4 * q + 3] += c.w * fv[q];
       }
     }
     reduce_scatter<G, 16>(acc);
@@ -161,14 +149,26 @@ __global__ void __launch_bounds__(kApThreads) k_apply_T_scatter(int64_t n,
 #pragma unroll
     for (int f = 0; f < 4; ++f) g[f] = ld4(gout + 4 * i + f);
     T cs[4] = {0, 0, 0, 0};
-    for (long long e = b + lane; e < e1; e += G) {
-      const int j = __ldg(col + e);
-      const V c = ld4(coef + e);
-      cs[0] += c.x; cs[1] += c.y; cs[2] += c.z; cs[3] += c.w;
-      T v[4];
+    constexpr int U = 4;   // entries per lane with their loads in flight together
+    for (long long e = b + lane; e < e1; e += U * G) {
+      int j[U];
+      V c[U];
 #pragma unroll
-      for (int f = 0; f < 4; ++f) v[f] = c.x * g[f].x + c.y * g[f].y + c.z * g[f].z + c.w * g[f].w;
-      add4<T>(gfields + j, v[0], v[1], v[2], v[3]);
+      for (int u = 0; u < U; ++u) {
+        const bool in = e + u * G < e1;
+        j[u] = in ? __ldg(col + e + u * G) : -1;
+        c[u] = in ? ld4(coef + e + u * G) : mk4<T>(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (j[u] < 0) break;
+        cs[0] += c[u].x; cs[1] += c[u].y; cs[2] += c[u].z; cs[3] += c[u].w;
+        T v[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          v[f] = c[u].x * g[f].x + c[u].y * g[f].y + c[u].z * g[f].z + c[u].w * g[f].w;
+        add4<T>(gfields + j[u], v[0], v[1], v[2], v[3]);
+      }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) cs[k] = group_sum<G>(cs[k]);
@@ -188,7 +188,7 @@ static void launch_apply(mafp_ctx *ctx, cudaStream_t s, int64_t n, const long lo
   using V = vec4_t<T>;
   const int G = ctx->tune.apply_group;
   const int blocks = grid_for(n * G, kApThreads, sm_count() * 64);
-  constexpr int U = sizeof(T) == 4 ? 4 : 2;
+  constexpr int U = sizeof(T) == 4 ? 8 : 2;
   const V *c = (const V *)coef, *f = (const V *)fields;
   T *o = (T *)out;
   if (G == 4) {
