@@ -489,7 +489,7 @@ __global__ void k_check_nnz(const long long *row_ptr, int64_t n, long long cap_n
 constexpr int kMaskThreads = 64;
 constexpr int kMaskTile = kMaskCap + kMaskWords;   // candidates plus one pad per word
 constexpr int kMaskMaxP = 512;                     // particles of one cell in the mask kernel
-constexpr int kExpThreads = 128;
+constexpr int kExpThreads = 256;
 constexpr int kExpChunk = 64;             // particles of a cell expanded per round
 
 // Rows of the 27-cell neighbourhood of global cell `key`: run r (dz = r/3-1,
