@@ -309,12 +309,7 @@ def bench_gpu(args):
              "apply_ops", "backward (field adjoint beside it)"]
     stage_ms = {nm: statistics.mean(m[k].elapsed_time(m[k + 1]) for m in stages)
                 for k, nm in enumerate(names)}
-    total_ms = sum(per_step)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    total_ms = max_over_ranks(sum(per_step), dev, world)
     ms_step = total_ms / args.steps
     value = world * n / (ms_step * 1e-3)
     st = ctx.status()
@@ -480,7 +475,7 @@ def bench_gpu(args):
             torch.cuda.synchronize()
             if it > 0:
                 tot += e0.elapsed_time(e1)
-        e2e_ms = tot / args.steps
+        e2e_ms = max_over_ranks(tot, dev, world) / args.steps
         e2e = {"value": round(world * n / (e2e_ms * 1e-3), 1), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": round(e2e_ms, 3),
@@ -719,6 +714,19 @@ def bench_tray(args):
                                              "n_deficient", "n_near")},
     }
     print(json.dumps(line), flush=True)
+
+
+def max_over_ranks(ms: float, device, world: int) -> float:
+    """The slowest rank's time (all ranks get it); the job's time for whole-job
+    throughput.  world == 1: returned as is."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
 
 
 def bench_reference(args):
