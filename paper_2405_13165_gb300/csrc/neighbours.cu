@@ -488,7 +488,12 @@ __global__ void k_check_nnz(const long long *row_ptr, int64_t n, long long cap_n
 // tests run once.
 constexpr int kMaskThreads = 64;
 constexpr int kMaskTile = kMaskCap + kMaskWords;   // candidates plus one pad per word
+// FP32 tile as four arrays (x, y, z, h/2), two pad floats per word of 32
+// candidates: a float2 read gives two consecutive candidates, and the words
+// that the threads of one warp test sit in different banks
+constexpr int kMaskTileSoA = kMaskCap + 2 * kMaskWords;
 constexpr int kMaskMaxP = 512;                     // particles of one cell in the mask kernel
+static_assert(kMaskCap < 65536 && kMaskMaxP % 2 == 0, "two 16-bit hit counts per word");
 constexpr int kExpThreads = 256;
 constexpr int kExpChunk = 64;             // particles of a cell expanded per round
 
@@ -544,8 +549,12 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
   using V = vec4_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *cand = reinterpret_cast<V *>(smem_raw);
+  float *tx = reinterpret_cast<float *>(smem_raw), *ty = tx + kMaskTileSoA,
+        *tz = ty + kMaskTileSoA, *th = tz + kMaskTileSoA;
   __shared__ int r_lo[9], r_len[9], r_off[10];
-  __shared__ int cnt_s[kMaskMaxP];
+  // per-particle hit counts, two 16-bit counts per word (a row has at most
+  // kMaskCap < 65536 candidates), so the FP32 tile and these fit 8 blocks per SM
+  __shared__ unsigned cnt_s[kMaskMaxP / 2];
   __shared__ int s_ovf;
   if (!cg.all->ok) return;
   const int tid = threadIdx.x;
@@ -572,13 +581,23 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
     if (!s_ovf) {
       // the tile holds candidate c at slot c + c / 32: one pad entry per word
       // puts the words that different threads test in different banks
+      // (FP32: slot c + 2 (c / 32) of four arrays, h halved)
       for (int r = 0; r < 9; ++r)
         for (int t = tid; t < r_len[r]; t += kMaskThreads) {
           const int c = r_off[r] + t;
-          cand[c + (c >> 5)] = ld4(spos + r_lo[r] + t);
+          const V v = ld4(spos + r_lo[r] + t);
+          if constexpr (sizeof(T) == 4) {
+            const int sl = c + 2 * (c >> 5);
+            tx[sl] = v.x;
+            ty[sl] = v.y;
+            tz[sl] = v.z;
+            th[sl] = 0.5f * v.w;   // exact: r = h_i / 2 + h_j / 2 = (h_i + h_j) / 2
+          } else {
+            cand[c + (c >> 5)] = v;
+          }
         }
       const int P = s1 - s0;
-      for (int q = tid; q < P; q += kMaskThreads) cnt_s[q] = 0;
+      for (int q = tid; q < (P + 1) / 2; q += kMaskThreads) cnt_s[q] = 0u;
       __syncthreads();
       const int nwords = (total + 31) >> 5;
       const int own = r_off[4] + (s0 - r_lo[4]);   // the cell's own particles, in run 4
@@ -588,24 +607,35 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
       for (int it = tid; it < items; it += kMaskThreads) {
         const int w = it / P, q = it - w * P;
         const int oc = own + q;
-        const V xi = cand[oc + (oc >> 5)];
         const int base = w << 5;
-        const V *cw = cand + base + w;           // slot of candidate 32 w
         const uint32_t valid = (total - base) >= 32 ? 0xffffffffu : ((1u << (total - base)) - 1u);
         uint32_t m = 0, band = 0;
         if constexpr (sizeof(T) == 4) {
-          // branch-free FP32 test of 32 candidates; the tile always holds
-          // 32 * nwords <= kMaskCap entries (plus pads), so reads past `total`
+          // two candidates per packed FP32 instruction; the tile always holds
+          // 32 * nwords <= kMaskCap slots (plus pads), so reads past `total`
           // stay in it and are masked off
+          const int so = oc + 2 * (oc >> 5);
+          const float2 nx = make_float2(-tx[so], -tx[so]), ny = make_float2(-ty[so], -ty[so]);
+          const float2 nz = make_float2(-tz[so], -tz[so]), hh = make_float2(th[so], th[so]);
+          const float2 klo = make_float2(0.99999f, 0.99999f), khi = make_float2(1.00001f, 1.00001f);
+          const int sb = base + 2 * w;   // slot of candidate 32 w
 #pragma unroll
-          for (int k = 0; k < 32; ++k) {
-            const float4 b = cw[k];
-            const float dx = b.x - xi.x, dy = b.y - xi.y, dz = b.z - xi.z;
-            const float d2 = (dx * dx + dy * dy) + dz * dz;
-            const float r = (xi.w + b.w) * 0.5f;
-            const float r2 = r * r;
-            m |= (d2 < r2 * 0.99999f ? 1u : 0u) << k;
-            band |= (d2 <= r2 * 1.00001f ? 1u : 0u) << k;
+          for (int k = 0; k < 32; k += 2) {
+            const float2 bx = *reinterpret_cast<const float2 *>(tx + sb + k);
+            const float2 by = *reinterpret_cast<const float2 *>(ty + sb + k);
+            const float2 bz = *reinterpret_cast<const float2 *>(tz + sb + k);
+            const float2 bh = *reinterpret_cast<const float2 *>(th + sb + k);
+            const float2 dx = __fadd2_rn(bx, nx), dy = __fadd2_rn(by, ny), dz = __fadd2_rn(bz, nz);
+            float2 d2 = __fmul2_rn(dx, dx);
+            d2 = __ffma2_rn(dy, dy, d2);
+            d2 = __ffma2_rn(dz, dz, d2);
+            const float2 r = __fadd2_rn(bh, hh);
+            const float2 r2 = __fmul2_rn(r, r);
+            const float2 lo = __fmul2_rn(r2, klo), hi = __fmul2_rn(r2, khi);
+            m |= (d2.x < lo.x ? 1u : 0u) << k;
+            m |= (d2.y < lo.y ? 1u : 0u) << (k + 1);
+            band |= (d2.x <= hi.x ? 1u : 0u) << k;
+            band |= (d2.y <= hi.y ? 1u : 0u) << (k + 1);
           }
           m &= valid;
           band &= valid & ~m;
@@ -613,19 +643,23 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
           while (band) {
             const int k = __ffs(band) - 1;
             band &= band - 1;
-            const float4 b = cw[k];
-            if (in_support64(xi.x, xi.y, xi.z, xi.w, b.x, b.y, b.z, b.w)) m |= 1u << k;
+            const int sl = sb + k;
+            if (in_support64(-nx.x, -ny.x, -nz.x, 2.0f * hh.x, tx[sl], ty[sl], tz[sl], 2.0f * th[sl]))
+              m |= 1u << k;
           }
         } else {
+          const V xi = cand[oc + (oc >> 5)];
+          const V *cw = cand + base + w;           // slot of candidate 32 w
           for (int k = 0; k < 32; ++k)
             if ((valid >> k) & 1u)
               if (support_test(xi, cw[k])) m |= 1u << k;
         }
         mask[(int64_t)w * stride + s0 + q] = m;
-        atomicAdd(&cnt_s[q], __popc(m));
+        atomicAdd(&cnt_s[q >> 1], (unsigned)__popc(m) << ((q & 1) * 16));
       }
       __syncthreads();
-      for (int q = tid; q < P; q += kMaskThreads) counts[svals[s0 + q]] = cnt_s[q];
+      for (int q = tid; q < P; q += kMaskThreads)
+        counts[svals[s0 + q]] = (int)((cnt_s[q >> 1] >> ((q & 1) * 16)) & 0xffffu);
     }
     __syncthreads();
   }
@@ -835,7 +869,9 @@ static int build_neighbours_t(mafp_ctx *ctx, int64_t n, int nb, const long long 
   int32_t *n_overflow = ctx->n_ucell + 1;
   const int64_t stride = ctx->cap_particles;
   MAFP_TIMED(ctx, s, sizeof(T) == 4 ? "k_nbr_mask<float>" : "k_nbr_mask<double>",
-             k_nbr_mask<T><<<sms * 16, kMaskThreads, kMaskTile * sizeof(V), s>>>(
+             k_nbr_mask<T><<<sms * 16, kMaskThreads,
+                             sizeof(T) == 4 ? 4 * kMaskTileSoA * sizeof(float) : kMaskTile * sizeof(V),
+                             s>>>(
                  cg, ctx->ucell, ctx->n_ucell, spos, vin, ctx->cell_start,
                  ctx->cell_end, ctx->counts, ctx->nbr_mask, stride, ctx->overflow, n_overflow));
   MAFP_TIMED(ctx, s, "k_nbr<T,false>(overflow cells)",
@@ -900,7 +936,7 @@ int build_neighbours_batched(mafp_ctx *ctx, int64_t n, int32_t dtype, int32_t nc
 
 void init_kernel_attributes() {
   cudaFuncSetAttribute(k_nbr_mask<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kMaskTile * (int)sizeof(float4));
+                       4 * kMaskTileSoA * (int)sizeof(float));
   cudaFuncSetAttribute(k_nbr_mask<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kMaskTile * (int)sizeof(double4_16a));
   cudaFuncSetAttribute(k_nbr<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
