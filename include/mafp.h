@@ -33,7 +33,7 @@ extern "C" {
 #define MAFP_ECAPACITY (-2)  /* a caller or context capacity is too small */
 #define MAFP_ECUDA (-3)      /* a CUDA runtime call failed (message in mafp_last_error) */
 #define MAFP_ETIMEOUT (-4)   /* a bounded device-side wait gave up */
-#define MAFP_ENOTIMPL (-5)   /* entry point not available in this build */
+#define MAFP_ENOTIMPL (-5)   /* entry point not implemented by this library */
 #define MAFP_ENONFINITE (-6) /* non-finite position or smoothing length seen on device */
 
 /* precision of a call */
