@@ -539,9 +539,18 @@ def bench_batched(args):
     from paper_2405_13165_gb300 import autotune, clouds as C, mafp as M
     from paper_2405_13165_gb300.pipeline import Pipeline, cloud_to_device
 
+    from paper_2405_13165_gb300 import shard
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
-    cloud, off = C.config_batched()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    # whole clouds per rank (no collective on the data path), longest first
+    parts = shard.assign_clouds(C.batched_sizes()[0], world)
+    cloud, off = C.config_batched(select=parts[rank])
     n, nb = cloud.n, len(off) - 1
     dtype = M.F32_REFINED
     ctx = M.Context(n)
@@ -589,9 +598,10 @@ def bench_batched(args):
     sampler = ClockSampler(dev.index)
     sampler.start()
     time.sleep(0.3)
-    ms_eager = timed(lambda: pipe.step(d, stream=s))
-    ms_graph = timed(graph.replay)
+    ms_eager = max_over_ranks(timed(lambda: pipe.step(d, stream=s)), dev, world)
+    ms_graph = max_over_ranks(timed(graph.replay), dev, world)
     clocks = sampler.stop()
+    n_all = int(sum_over_ranks(n, dev, world))
     st = ctx.status()
     if st["code"] != 0:
         raise RuntimeError(f"device status after the batched passes: {st}")
@@ -615,17 +625,21 @@ def bench_batched(args):
     sizes = np.diff(off)
     line = {
         "metric": "particles/s for neighbour+PCA+stencil build+apply over a batch of clouds",
-        "value": round(n / (ms_graph * 1e-3), 1), "unit": UNIT, "n_gpus": 1,
+        "value": round(n_all / (ms_graph * 1e-3), 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_graph, 4),
-        "ms_per_step_eager": round(ms_eager, 4), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step_eager": round(ms_eager, 4), "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded cube-on-sheet clouds)",
         "config": {"workload": f"batch of {nb} independent cube-on-sheet clouds, sizes log-uniform "
                                f"2k-200k, film fraction U[0.1, 0.9], dx = 0.02 m",
-                   "n_particles": n, "nnz": nnz, "clouds": nb, "smallest": int(sizes.min()),
+                   "n_particles": n_all, "n_particles_rank0": n, "nnz_rank0": nnz,
+                   "clouds": len(C.batched_sizes()[0]), "clouds_rank0": nb,
+                   "smallest": int(sizes.min()),
                    "largest": int(sizes.max()), "n_2d": int((cloud.model == 1).sum()),
                    "step": "batched neighbours, detection, stencils, apply (CUDA graph replay)",
                    "l2": "flushed (256 MB write) before every timed pass",
-                   "parallelism": "single GPU"},
+                   "parallelism": (f"{world} ranks, whole clouds per rank (longest first)"
+                                   if world > 1 else "single GPU")},
         "roofline": roof, "tuning": tuned, "clocks": clocks,
         "gpu_launches": int(launches * args.steps),
         "kernel_profile_top": [{"kernel": k, "launches": v[0],
@@ -634,7 +648,12 @@ def bench_batched(args):
         "device_status": {k: st[k] for k in ("code", "n_fp64_stencil", "n_fp64_eigen",
                                              "n_deficient", "n_near", "cells_identity")},
     }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def bench_tray(args):
@@ -726,6 +745,17 @@ def max_over_ranks(ms: float, device, world: int) -> float:
     t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.barrier()
+    return float(t.item())
+
+
+def sum_over_ranks(v: float, device, world: int) -> float:
+    """Sum of a per-rank count over the ranks (all ranks get it)."""
+    if world <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 

@@ -369,9 +369,19 @@ def config_diff_2m(seed: int = SEED_BASE + 4) -> Cloud:
     return cube_on_sheet(mid, seed=seed)
 
 
+def batched_sizes(nclouds: int = 256, n_lo: int = 2_000, n_hi: int = 200_000,
+                  film_lo: float = 0.1, film_hi: float = 0.9,
+                  seed: int = SEED_BASE + 3) -> tuple[np.ndarray, np.ndarray]:
+    """The draws behind `batched_clouds`: target sizes N_b and film fractions f_b."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=nclouds))
+    films = rng.uniform(film_lo, film_hi, size=nclouds)
+    return sizes, films
+
+
 def batched_clouds(nclouds: int = 256, n_lo: int = 2_000, n_hi: int = 200_000,
                    film_lo: float = 0.1, film_hi: float = 0.9, dx: float = 0.02,
-                   seed: int = SEED_BASE + 3) -> list[Cloud]:
+                   seed: int = SEED_BASE + 3, select=None) -> list[Cloud]:
     """Independent cube-on-sheet clouds of uneven size and model mix.
 
     Cloud b draws N_b log-uniform in [n_lo, n_hi] and a film fraction f_b
@@ -380,22 +390,22 @@ def batched_clouds(nclouds: int = 256, n_lo: int = 2_000, n_hi: int = 200_000,
     s = round(sqrt(f_b N_b + m^2)) cells.  Its lattice, jitter and fields use
     seed 1000 * 3 + b above the base seed.  Every cloud sits at the same place,
     so clouds overlap in space and only the batching keeps them apart.
+    select: the indices b to build (default all), each cloud as in the full batch.
     """
-    rng = np.random.default_rng(seed)
-    sizes = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=nclouds))
-    films = rng.uniform(film_lo, film_hi, size=nclouds)
+    sizes, films = batched_sizes(nclouds, n_lo, n_hi, film_lo, film_hi, seed)
     out = []
-    for b in range(nclouds):
+    for b in (range(nclouds) if select is None else select):
         m = max(2, int(round(((1.0 - films[b]) * sizes[b]) ** (1.0 / 3.0))))
         s = max(m + 2, int(round(math.sqrt(films[b] * sizes[b] + m * m))))
         out.append(cube_on_sheet(dx, cube=m * dx, sheet=s * dx, seed=SEED_BASE + 3 * 1000 + b))
     return out
 
 
-def config_batched(nclouds: int = 256, **kw) -> tuple[Cloud, np.ndarray]:
+def config_batched(nclouds: int = 256, select=None, **kw) -> tuple[Cloud, np.ndarray]:
     """The batched workload: `batched_clouds` each put in its own cell order and
-    stored back to back; returns (cloud, int64 offsets [nclouds + 1])."""
-    parts = [cell_sorted(c) for c in batched_clouds(nclouds, **kw)]
+    stored back to back; returns (cloud, int64 offsets [clouds + 1]).  select:
+    only those clouds (in the given order), e.g. one rank's share."""
+    parts = [cell_sorted(c) for c in batched_clouds(nclouds, select=select, **kw)]
     off = np.zeros(len(parts) + 1, np.int64)
     off[1:] = np.cumsum([c.n for c in parts])
     return concat(parts, f"batched({len(parts)} clouds)"), off
