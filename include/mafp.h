@@ -78,8 +78,9 @@ typedef struct {
   int32_t stencil2d_group; /* lanes per 2D particle in mafp_build_stencils: 4, 8 or 16 */
   int32_t apply_group;     /* lanes per row in mafp_apply_ops / _backward: 4, 8 or 16 */
   int32_t grad3d_group;    /* lanes per 3D particle in mafp_build_stencils_backward: 4, 8,
-                              16 or 32 (the FP64 adjoint takes at least 8; 2D particles
-                              there use stencil2d_group) */
+                              16 or 32 (the FP64 adjoint takes at least 8) */
+  int32_t grad2d_group;    /* lanes per 2D particle in mafp_build_stencils_backward: 2, 4,
+                              8 or 16 */
 } mafp_tuning;
 
 /* Device-side status block, copied out by mafp_get_status. */

@@ -18,7 +18,8 @@ from . import mafp as M
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
 CHOICES = {"stencil3d_group": (8, 16, 32), "stencil2d_group": (4, 8, 16),
-           "apply_group": (4, 8, 16), "grad3d_group": (4, 8, 16, 32)}
+           "apply_group": (4, 8, 16), "grad3d_group": (4, 8, 16, 32),
+           "grad2d_group": (2, 4, 8, 16)}
 
 
 def mix_key(d, pipe, n: int) -> str:
@@ -77,14 +78,15 @@ def tune(ctx: M.Context, pipe, d, use_cache: bool = True, verbose: bool = False)
     pipe.apply(d)
     gout = pipe.out[:n].clone()
     gpos = torch.empty_like(d["pos_h"])
-    res = {}
-    for g in CHOICES["grad3d_group"]:
-        ctx.set_tuning(**{**best, "grad3d_group": g})
-        res[g] = _time(lambda: M.build_stencils_backward(
-            ctx, d["pos_h"], d["model"], pipe.frame[:n], pipe.row_ptr[: n + 1], pipe.col,
-            d["fields"], gout, gpos, pipe.dtype))
-    best["grad3d_group"] = min(res, key=res.get)
-    timings["grad3d_group"] = res
+    for knob in ("grad3d_group", "grad2d_group"):
+        res = {}
+        for g in CHOICES[knob]:
+            ctx.set_tuning(**{**best, knob: g})
+            res[g] = _time(lambda: M.build_stencils_backward(
+                ctx, d["pos_h"], d["model"], pipe.frame[:n], pipe.row_ptr[: n + 1], pipe.col,
+                d["fields"], gout, gpos, pipe.dtype))
+        best[knob] = min(res, key=res.get)
+        timings[knob] = res
     ctx.set_tuning(**best)
     entry = {"tuning": best, "timings_ms": {k: {str(g): round(v, 4) for g, v in r.items()}
                                             for k, r in timings.items()}, "key": key}

@@ -128,6 +128,7 @@ int mafp_create(mafp_ctx **out, const mafp_params *params, int64_t cap_particles
   ctx->tune.stencil2d_group = 8;
   ctx->tune.apply_group = 8;
   ctx->tune.grad3d_group = 4;
+  ctx->tune.grad2d_group = 2;
   ctx->cap_particles = cap_particles;
   ctx->cap_cells = cap_cells;
   cudaGetDevice(&ctx->device);
@@ -209,11 +210,12 @@ const char *mafp_last_error(const mafp_ctx *ctx) { return ctx ? ctx->err : kNoCt
 int mafp_set_tuning(mafp_ctx *ctx, const mafp_tuning *t) {
   if (!ctx || !t) return MAFP_EINVAL;
   const int g3 = t->stencil3d_group, g2 = t->stencil2d_group, ga = t->apply_group;
-  const int gb = t->grad3d_group;
+  const int gb = t->grad3d_group, gf = t->grad2d_group;
   if (!(g3 == 8 || g3 == 16 || g3 == 32)) return fail(ctx, MAFP_EINVAL, "stencil3d_group");
   if (!(g2 == 4 || g2 == 8 || g2 == 16)) return fail(ctx, MAFP_EINVAL, "stencil2d_group");
   if (!(ga == 4 || ga == 8 || ga == 16)) return fail(ctx, MAFP_EINVAL, "apply_group");
   if (!(gb == 4 || gb == 8 || gb == 16 || gb == 32)) return fail(ctx, MAFP_EINVAL, "grad3d_group");
+  if (!(gf == 2 || gf == 4 || gf == 8 || gf == 16)) return fail(ctx, MAFP_EINVAL, "grad2d_group");
   ctx->tune = *t;
   return MAFP_OK;
 }

@@ -76,6 +76,7 @@ extern "C" int mafp_build_stencils_noalloc(int64_t n, int32_t dtype, const mafp_
   c.tune.stencil2d_group = 8;
   c.tune.apply_group = 8;
   c.tune.grad3d_group = 4;
+  c.tune.grad2d_group = 2;
   c.cap_particles = kNoAllocMaxParticles;
   c.device = dev;
   c.fallback = scr->queue;

@@ -313,7 +313,7 @@ static void launch_grad_g(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void *
 }
 
 // Group sizes: grad3d_group for 3D particles (at least 8 in FP64, where the
-// 4-lane instance would spill its registers), stencil2d_group for 2D ones.
+// 4-lane instance would spill its registers), grad2d_group for 2D ones.
 template <typename TS, typename C, bool QUEUE>
 static void launch_grad(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void *pos_h,
                         const uint8_t *model, const void *frame, const long long *rp,
@@ -330,7 +330,8 @@ static void launch_grad(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void *po
     case 16: launch_grad_g<TS, C, 10, 16, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
     default: launch_grad_g<TS, C, 10, 32, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
   }
-  switch (ctx->tune.stencil2d_group) {
+  switch (ctx->tune.grad2d_group) {
+    case 2: launch_grad_g<TS, C, 6, 2, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
     case 4: launch_grad_g<TS, C, 6, 4, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
     case 16: launch_grad_g<TS, C, 6, 16, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
     default: launch_grad_g<TS, C, 6, 8, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
