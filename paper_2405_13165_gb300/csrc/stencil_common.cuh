@@ -71,6 +71,38 @@ struct Moments {
 };
 static_assert(Moments<10>::N == 35 && Moments<6>::N == 15, "distinct moments of degree <= 4");
 
+// Every entry (r, c) reads a moment whose representative pair multiplies to the
+// same monomial, and distinct moments are distinct monomials (checked while
+// compiling, from the exponents written out again here).
+template <int M>
+constexpr bool moment_table_consistent() {
+  int e[10][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                  {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+  if (M == 6) {
+    const int e2[6][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {2, 0, 0}, {1, 1, 0}, {0, 2, 0}};
+    for (int r = 0; r < 6; ++r)
+      for (int a = 0; a < 3; ++a) e[r][a] = e2[r][a];
+  }
+  constexpr MomentTable<M> T = make_moment_table<M>();
+  for (int r = 0; r < M; ++r)
+    for (int c = 0; c <= r; ++c) {
+      const int m = T.idx[r * (r + 1) / 2 + c];
+      if (m < 0 || m >= T.n) return false;
+      for (int a = 0; a < 3; ++a)
+        if (e[r][a] + e[c][a] != e[T.rep_r[m]][a] + e[T.rep_c[m]][a]) return false;
+    }
+  for (int m = 0; m < T.n; ++m)
+    for (int k = 0; k < m; ++k) {
+      bool same = true;
+      for (int a = 0; a < 3; ++a)
+        same = same && (e[T.rep_r[m]][a] + e[T.rep_c[m]][a] == e[T.rep_r[k]][a] + e[T.rep_c[k]][a]);
+      if (same) return false;
+    }
+  return true;
+}
+static_assert(moment_table_consistent<10>() && moment_table_consistent<6>(),
+              "moment table: entries and representatives disagree");
+
 // Add w p p^T of one neighbour to the distinct moments.
 template <int M, typename C, int VM>
 __device__ __forceinline__ void add_moments(C (&mom)[VM], C w, const C (&p)[M]) {
