@@ -22,6 +22,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum { M3D = 0, M2D = 1 };
 enum { T_INT = 0, T_FS = 1, T_WALL = 2 };
@@ -222,28 +225,36 @@ void orc_jacobi3(const double Ain[9], double lam[3], double V[9]) {
  * shifted by x_i and divided by h_i, which scales every eigenvalue by 1/h_i^2
  * and leaves ratios and eigenvectors unchanged.
  * ------------------------------------------------------------------------- */
-int64_t orc_pca(const double *P, const uint8_t *model, const int64_t *row_ptr,
-                const int32_t *col, int64_t i, double lam[3], double V[9]) {
-  double h = P[4 * i + 3], xc[3] = {0, 0, 0};
+static int64_t pca_scatter(const double *P, const uint8_t *model, const int64_t *row_ptr,
+                           const int32_t *col, int64_t i, double yc[3], double C[9]) {
+  double h = P[4 * i + 3];
   int64_t m = 0;
+  for (int a = 0; a < 3; ++a) yc[a] = 0.0;
+  for (int k = 0; k < 9; ++k) C[k] = 0.0;
   for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
     int64_t j = col[e];
     if (model[j] != model[i]) continue;
-    for (int a = 0; a < 3; ++a) xc[a] += (P[4 * j + a] - P[4 * i + a]) / h;
+    for (int a = 0; a < 3; ++a) yc[a] += (P[4 * j + a] - P[4 * i + a]) / h;
     ++m;
   }
-  double C[9] = {0};
   if (m > 0) {
-    for (int a = 0; a < 3; ++a) xc[a] /= (double)m;
+    for (int a = 0; a < 3; ++a) yc[a] /= (double)m;
     for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
       int64_t j = col[e];
       if (model[j] != model[i]) continue;
       double d[3];
-      for (int a = 0; a < 3; ++a) d[a] = (P[4 * j + a] - P[4 * i + a]) / h - xc[a];
+      for (int a = 0; a < 3; ++a) d[a] = (P[4 * j + a] - P[4 * i + a]) / h - yc[a];
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) C[a * 3 + b] += d[a] * d[b];
     }
   }
+  return m;
+}
+
+int64_t orc_pca(const double *P, const uint8_t *model, const int64_t *row_ptr,
+                const int32_t *col, int64_t i, double lam[3], double V[9]) {
+  double yc[3], C[9];
+  int64_t m = pca_scatter(P, model, row_ptr, col, i, yc, C);
   orc_jacobi3(C, lam, V);
   return m;
 }
@@ -539,13 +550,32 @@ void orc_stencils(int64_t n, const double *P, const uint8_t *model, const int64_
  *   s_jk = p_j.lambda_k,  t_jk = p_j.mu_k,
  *   wbar_j = sum_k (gbar_jk - t_jk) s_jk,
  *   pbar_j = w_j sum_k (gbar_jk lambda_k - s_jk mu_k - t_jk lambda_k),
- * then through p(q) and w(|q|) to q_j = (x_j - x_i)/h_i.  Neighbour sets,
- * models and (for film rows) the tangent frame are held fixed.
+ * then through p(q) and w(|q|) to q_j = (x_j - x_i)/h_i.  Neighbour sets and
+ * models are held fixed (piecewise constant in the positions).
+ *
+ * Film rows also depend on the positions through their tangent frame, the
+ * local PCA of Sec. 4.1.2 that stencil_one recomputes: t1 = w1, t2 = w2 of the
+ * scatter matrix Ps = sum_j z_j z_j^T, z_j = y_j - y_c, y_j = (x_j - x_i)/h_i,
+ * y_c the centroid.  The outputs (tangential gradient c^xi t1 + c^eta t2 and
+ * the plane Laplacian) do not change when (t1, t2) turn inside the plane, so
+ * only the normal n = w3 matters.  With tbar_k = dL/dt_k at fixed n, turning
+ * the frame with n (dt_k = -n (t_k . dn)) gives dL = -sum_k (tbar_k . n)(t_k . dn);
+ * first-order perturbation of the eigenvector w3,
+ *   dn = -sum_{k=1,2} w_k (w_k^T dPs n) / (l_k - l3),
+ * and dPs = sum_j (dy_j z_j^T + z_j dy_j^T) (the centroid terms cancel since
+ * sum_j z_j = 0) give
+ *   ybar_j = sum_k beta_k (t_k (n . z_j) + n (t_k . z_j)),
+ *   beta_k = (tbar_k . n) / (l_k - l3),
+ * passed to x_j and x_i like the stencil terms.
  * ------------------------------------------------------------------------- */
 static double weight_dw_over_s(double s, double alpha) {
   /* W'(s)/s for s <= 1 (W of weight_w), 0 outside the support */
   if (s > 1.0) return 0.0;
   return -2.0 * alpha * exp(-alpha * s * s) / (1.0 - exp(-alpha));
+}
+
+static double dot3(const double a[3], const double b[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
 static void stencil_grad_one(int64_t i, const double *P, const uint8_t *model,
@@ -554,11 +584,17 @@ static void stencil_grad_one(int64_t i, const double *P, const uint8_t *model,
   const int is2d = model[i] == M2D;
   const int m = is2d ? 6 : 10, nr = is2d ? 3 : 4;
   const double h = P[4 * i + 3];
-  double t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0};
+  double t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0}, nv[3] = {0, 0, 0};
+  double plam[3] = {0, 0, 0}, yc[3] = {0, 0, 0};
   if (is2d) {
-    double lam[3], V[9];
-    orc_pca(P, model, row_ptr, col, i, lam, V);
-    for (int a = 0; a < 3; ++a) { t1[a] = V[a * 3 + 0]; t2[a] = V[a * 3 + 1]; }
+    double V[9], Ps[9];
+    pca_scatter(P, model, row_ptr, col, i, yc, Ps);
+    orc_jacobi3(Ps, plam, V);
+    for (int a = 0; a < 3; ++a) {
+      t1[a] = V[a * 3 + 0];
+      t2[a] = V[a * 3 + 1];
+      nv[a] = V[a * 3 + 2];
+    }
   }
   double A[100] = {0}, p[10];
   int64_t cnt = 0;
@@ -569,8 +605,7 @@ static void stencil_grad_one(int64_t i, const double *P, const uint8_t *model,
     for (int a = 0; a < 3; ++a) d[a] = P[4 * j + a] - P[4 * i + a];
     double w = weight_w(sqrt(dist2(P, i, j)) / h, prm->alpha_w);
     if (is2d) {
-      basis2((d[0] * t1[0] + d[1] * t1[1] + d[2] * t1[2]) / h,
-             (d[0] * t2[0] + d[1] * t2[1] + d[2] * t2[2]) / h, p);
+      basis2(dot3(d, t1) / h, dot3(d, t2) / h, p);
     } else {
       for (int a = 0; a < 3; ++a) q[a] = d[a] / h;
       basis3(q, p);
@@ -592,6 +627,8 @@ static void stencil_grad_one(int64_t i, const double *P, const uint8_t *model,
     b[3][4] = 2.0 / (h * h); b[3][5] = 2.0 / (h * h); b[3][6] = 2.0 / (h * h);
   }
   for (int k = 0; k < nr; ++k) chol_solve(m, A, b[k], lam[k]);
+  /* dL/dt_k of a film row at fixed n, summed over the row */
+  double tbar[2][3] = {{0, 0, 0}, {0, 0, 0}};
   /* dL/dc for the row: gbar_jk = sum_f gout[i][f][op] (u_j - u_i); for a film row
    * the gradient outputs are c^xi t1 + c^eta t2, so gbar^xi = gbar . t1, etc. */
   for (int pass = 0; pass < 2; ++pass) {
@@ -606,8 +643,8 @@ static void stencil_grad_one(int64_t i, const double *P, const uint8_t *model,
       }
       double gb[4];
       if (is2d) {
-        gb[0] = g4[0] * t1[0] + g4[1] * t1[1] + g4[2] * t1[2];
-        gb[1] = g4[0] * t2[0] + g4[1] * t2[1] + g4[2] * t2[2];
+        gb[0] = dot3(g4, t1);
+        gb[1] = dot3(g4, t2);
         gb[2] = g4[3];
       } else {
         for (int k = 0; k < 4; ++k) gb[k] = g4[k];
@@ -618,8 +655,8 @@ static void stencil_grad_one(int64_t i, const double *P, const uint8_t *model,
       double w = weight_w(s_, prm->alpha_w);
       double xi = 0, eta = 0;
       if (is2d) {
-        xi = (d[0] * t1[0] + d[1] * t1[1] + d[2] * t1[2]) / h;
-        eta = (d[0] * t2[0] + d[1] * t2[1] + d[2] * t2[2]) / h;
+        xi = dot3(d, t1) / h;
+        eta = dot3(d, t2) / h;
         basis2(xi, eta, p);
       } else {
         for (int a = 0; a < 3; ++a) q[a] = d[a] / h;
@@ -648,6 +685,12 @@ static void stencil_grad_one(int64_t i, const double *P, const uint8_t *model,
         double xib = pbar[1] + 2.0 * xi * pbar[3] + eta * pbar[4];
         double etb = pbar[2] + xi * pbar[4] + 2.0 * eta * pbar[5];
         for (int a = 0; a < 3; ++a) dbar[a] = (xib * t1[a] + etb * t2[a]) / h + wq * d[a] / (h * h);
+        /* the frame enters through xi = d.t1/h, eta = d.t2/h and through the
+         * world-coordinate gradient c^xi t1 + c^eta t2 (c^xi = w s_0, c^eta = w s_1) */
+        for (int a = 0; a < 3; ++a) {
+          tbar[0][a] += xib * d[a] / h + g4[a] * w * sk[0];
+          tbar[1][a] += etb * d[a] / h + g4[a] * w * sk[1];
+        }
       } else {
         double qb[3];
         qb[0] = pbar[1] + 2.0 * q[0] * pbar[4] + q[1] * pbar[7] + q[2] * pbar[8];
@@ -663,20 +706,70 @@ static void stencil_grad_one(int64_t i, const double *P, const uint8_t *model,
     if (pass == 0)
       for (int k = 0; k < nr; ++k) chol_solve(m, A, lbar[k], mu[k]);
   }
+  if (!is2d) return;
+  /* film frame: through n = w3 of the local PCA to the scaled positions y_j.
+   * A gap l_k - l3 of zero leaves w3 undefined: no term is taken then. */
+  double beta[2];
+  for (int k = 0; k < 2; ++k) {
+    double gap = plam[k] - plam[2];
+    beta[k] = gap > 0.0 ? dot3(tbar[k], nv) / gap : 0.0;
+  }
+  const double *tk_[2] = {t1, t2};
+  for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+    int64_t j = col[e];
+    if (model[j] != model[i]) continue;
+    double z[3], ybar[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) z[a] = (P[4 * j + a] - P[4 * i + a]) / h - yc[a];
+    double nz = dot3(nv, z);
+    for (int k = 0; k < 2; ++k) {
+      double tz = dot3(tk_[k], z);
+      for (int a = 0; a < 3; ++a) ybar[a] += beta[k] * (tk_[k][a] * nz + nv[a] * tz);
+    }
+    for (int a = 0; a < 3; ++a) {
+      gpos[4 * j + a] += ybar[a] / h;
+      gpos[4 * i + a] -= ybar[a] / h;
+    }
+  }
 }
 
+/* Rows are dealt to the threads in fixed chunks; each thread sums into its own
+ * buffer and the buffers are added in thread order (deterministic for a given
+ * thread count). */
 void orc_stencil_grad(int64_t n, const double *P, const uint8_t *model, const int64_t *row_ptr,
                       const int32_t *col, const orc_params *prm, const double *fields,
                       const double *gout, double *gpos) {
   for (int64_t k = 0; k < 4 * n; ++k) gpos[k] = 0.0;
-  for (int64_t i = 0; i < n; ++i) {
-    /* a row whose 16 output gradients are all zero contributes exactly zero
-       (every term of its adjoint is a product with gbar = 0): skip it */
-    int live = 0;
-    for (int k = 0; k < 16; ++k) live |= gout[16 * i + k] != 0.0;
-    if (!live) continue;
-    stencil_grad_one(i, P, model, row_ptr, col, prm, fields, gout, gpos);
+  if (n <= 0) return;
+  int nth = 1;
+#ifdef _OPENMP
+  nth = omp_get_max_threads();
+#endif
+  double *buf = (double *)calloc((size_t)nth * (size_t)(4 * n), sizeof(double));
+  if (!buf) return;
+#pragma omp parallel num_threads(nth)
+  {
+    int t = 0;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+#endif
+    double *g = buf + (size_t)t * (size_t)(4 * n);
+#pragma omp for schedule(static, 64)
+    for (int64_t i = 0; i < n; ++i) {
+      /* a row whose 16 output gradients are all zero contributes exactly zero
+         (every term of its adjoint is a product with gbar = 0): skip it */
+      int live = 0;
+      for (int k = 0; k < 16; ++k) live |= gout[16 * i + k] != 0.0;
+      if (!live) continue;
+      stencil_grad_one(i, P, model, row_ptr, col, prm, fields, gout, g);
+    }
   }
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < 4 * n; ++k) {
+    double s = 0.0;
+    for (int t = 0; t < nth; ++t) s += buf[(size_t)t * (size_t)(4 * n) + k];
+    gpos[k] = s;
+  }
+  free(buf);
 }
 
 /* Eq. GFDM_Definition: d*_i u = sum_{j in S_i} c*_ij u_j, for the four fields. */

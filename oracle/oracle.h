@@ -83,7 +83,8 @@ void orc_stencils(int64_t n, const double *P, const uint8_t *model, const int64_
 /* Gradient of a loss L(out) with respect to the positions x (gpos [n][4],
  * h component 0) through the stencils of orc_stencils, given
  * gout = dL/dout [n][4][4] and the fields; out_i = sum_j c_ij (u_j - u_i).
- * Neighbour sets, models and film tangent frames are held fixed. */
+ * Neighbour sets and models are held fixed; film rows include the dependence
+ * of their tangent frame (the local PCA of Sec. 4.1.2) on the positions. */
 void orc_stencil_grad(int64_t n, const double *P, const uint8_t *model, const int64_t *row_ptr,
                       const int32_t *col, const orc_params *prm, const double *fields,
                       const double *gout, double *gpos);
@@ -103,11 +104,12 @@ int64_t orc_remap(int64_t n, const orc_state *in, const uint8_t *flag, const int
                   const int32_t *col, const orc_params *prm, orc_state *out, int64_t cap_out,
                   int32_t *old2new);
 
-#ifdef __cplusplus
-}
-#endif
 /* Alg. 5, first loop: src[i] = 1 when S_i holds a particle of the other model. */
 void orc_ghost_sources(int64_t n, const uint8_t *model, const int64_t *row_ptr,
                        const int32_t *col, uint8_t *src);
+
+#ifdef __cplusplus
+}
+#endif
 
 #endif

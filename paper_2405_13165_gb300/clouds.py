@@ -325,6 +325,57 @@ def flat_film(dx: float, extent: float, film_h: float, seed: int = SEED_BASE + 8
     return c
 
 
+def rotation(axis, angle: float) -> np.ndarray:
+    """3x3 rotation matrix about the unit direction of `axis` by `angle` (rad)."""
+    k = np.asarray(axis, np.float64)
+    k = k / np.linalg.norm(k)
+    K = np.array([[0.0, -k[2], k[1]], [k[2], 0.0, -k[0]], [-k[1], k[0], 0.0]])
+    return np.eye(3) + math.sin(angle) * K + (1.0 - math.cos(angle)) * (K @ K)
+
+
+def rotated(cloud: Cloud, axis=(1.0, 0.4, 0.0), angle: float = 0.5) -> Cloud:
+    """The cloud turned rigidly about `axis` through the origin (positions and
+    normals; positions rounded to float32 again, so a tilted film is planar
+    only up to that rounding)."""
+    R = rotation(axis, angle)
+    c = cloud.take(np.arange(cloud.n))
+    c.pos_h[:, :3] = (cloud.pos_h[:, :3].astype(np.float64) @ R.T).astype(np.float32)
+    c.normal[:, :3] = (cloud.normal[:, :3].astype(np.float64) @ R.T).astype(np.float32)
+    c.name = f"rotated({cloud.name})"
+    return c
+
+
+def curved_film(dx: float, r_disc: float, radius: float, film_h: float | None = None,
+                seed: int = SEED_BASE + 9, h_factor: float = 3.5) -> Cloud:
+    """One layer of 2D film particles on a spherical cap: the points of a square
+    lattice (u, v) at spacing dx within the disc u^2 + v^2 <= r_disc^2 (r_disc <
+    radius), jittered +-0.1 dx in u and v, lifted to z = R - sqrt(R^2 - u^2 - v^2)
+    (on the sphere of radius R centred at (0, 0, R)); inward normal towards the
+    centre."""
+    assert 0.0 < r_disc < radius
+    rng = np.random.default_rng(seed)
+    n = int(math.floor(r_disc / dx))
+    ii, jj = np.meshgrid(np.arange(-n, n + 1), np.arange(-n, n + 1), indexing="ij")
+    u0, v0 = ii.ravel() * dx, jj.ravel() * dx
+    keep = u0 * u0 + v0 * v0 <= (r_disc - 0.1 * dx) ** 2
+    u0, v0 = u0[keep], v0[keep]
+    u = u0 + rng.uniform(-0.1 * dx, 0.1 * dx, u0.size)
+    v = v0 + rng.uniform(-0.1 * dx, 0.1 * dx, v0.size)
+    z = radius - np.sqrt(radius * radius - u * u - v * v)
+    xyz = np.stack([u, v, z], 1)
+    ctr = np.array([0.0, 0.0, radius])
+    nrm = (ctr[None, :] - xyz) / np.linalg.norm(ctr[None, :] - xyz, axis=1)[:, None]
+    model = np.full(xyz.shape[0], MODEL_2D, np.uint8)
+    ptype = np.full(xyz.shape[0], TYPE_WALL, np.uint8)
+    normal = np.zeros((xyz.shape[0], 4), np.float32)
+    normal[:, :3] = nrm
+    c = _finish(xyz, model, ptype, normal, 0.3 * dx if film_h is None else film_h, dx, rng,
+                f"curved_film(dx={dx:g}, R={radius:g})")
+    c.pos_h[:, 3] = np.float32(h_factor * dx)
+    c.h3d[:] = np.float32(h_factor * dx)
+    return c
+
+
 def random_cloud(n: int, seed: int, box: float = 1.0, h_lo: float = 0.08, h_hi: float = 0.12,
                  frac2d: float = 0.3) -> Cloud:
     """Unstructured cloud with variable h and random models/types (edge cases)."""

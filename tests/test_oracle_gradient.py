@@ -1,5 +1,6 @@
 """Pins of the oracle's position gradient through the GFDM stencils against
-central finite differences in FP64 (neighbour sets held fixed)."""
+central finite differences in FP64 (neighbour sets held fixed), on flat,
+tilted and curved films, every coordinate of the film particles included."""
 import numpy as np
 import pytest
 
@@ -20,9 +21,23 @@ def _safe_coords(P, rp, col, i, step):
     return np.all(np.abs(d - P[i, 3]) > 10 * step)
 
 
+def _shape(name):
+    """Flat, tilted and curved films (the last two with film rows whose
+    neighbours lie off their tangent plane), with a 3D cube where there is one."""
+    if name == "flat":
+        return C.cube_on_sheet(0.05, cube=0.4, sheet=1.0), 0.05      # 512 + 384 particles
+    if name == "tilted":
+        return C.rotated(C.cube_on_sheet(0.05, cube=0.4, sheet=1.0), (1.0, 0.4, 0.2), 0.6), 0.05
+    cap = C.curved_film(0.05, 0.55, 0.7)
+    cube = C.cube_on_sheet(0.05, cube=0.25, sheet=0.35)
+    cube.pos_h[:, 2] += 0.5    # lifted clear of the cap
+    return C.concat([cap, cube]), 0.05
+
+
+@pytest.mark.parametrize("shape", ["flat", "tilted", "curved"])
 @pytest.mark.parametrize("loss", ["laplacian", "random"])
-def test_gradient_matches_central_differences(orc, loss):
-    c = C.cube_on_sheet(0.05, cube=0.4, sheet=1.0)   # 512 + 384 particles
+def test_gradient_matches_central_differences(orc, loss, shape):
+    c, dx = _shape(shape)
     P = c.pos_h.astype(np.float64)
     F = c.vp.astype(np.float64)
     rp, col = orc.neighbours(P)
@@ -36,33 +51,60 @@ def test_gradient_matches_central_differences(orc, loss):
     else:
         G = rng.normal(size=out.shape)
     g = orc.stencil_grad(P, c.model, rp, col, F, G)
-    dx = 0.05
     step = 1e-4 * dx
-    picks = rng.choice(c.n, 60, replace=False)
-    checked = 0
+    # film particles first: every coordinate of theirs moves the PCA frame of
+    # the film rows around them
+    film = np.nonzero(c.model == 1)[0]
+    bulk = np.nonzero(c.model == 0)[0]
+    picks = np.concatenate([rng.choice(film, 40, replace=False),
+                            rng.choice(bulk, min(20, bulk.size), replace=False)])
+    checked = film_z = 0
     for i in picks:
         if not _safe_coords(P, rp, col, i, step):
             continue
-        # film rows hold their tangent frame fixed: the out-of-plane coordinate of
-        # a film particle is checked only for the Laplacian loss (first-order exact)
-        axes = (0, 1, 2) if (c.model[i] == 0 or loss == "laplacian") else (0, 1)
-        for a in axes:
-            Pp = P.copy()
-            Pm = P.copy()
-            Pp[i, a] += step
-            Pm[i, a] -= step
-            if loss == "laplacian":
-                lp = np.sum(_loss(orc, Pp, c.model, rp, col, F, G)[1][:, :, 3] ** 2)
-                lm = np.sum(_loss(orc, Pm, c.model, rp, col, F, G)[1][:, :, 3] ** 2)
-            else:
-                lp = _loss(orc, Pp, c.model, rp, col, F, G)[0]
-                lm = _loss(orc, Pm, c.model, rp, col, F, G)[0]
-            fd = (lp - lm) / (2 * step)
+        for a in (0, 1, 2):
+            def central(st):
+                Pp = P.copy()
+                Pm = P.copy()
+                Pp[i, a] += st
+                Pm[i, a] -= st
+                if loss == "laplacian":
+                    lp = np.sum(_loss(orc, Pp, c.model, rp, col, F, G)[1][:, :, 3] ** 2)
+                    lm = np.sum(_loss(orc, Pm, c.model, rp, col, F, G)[1][:, :, 3] ** 2)
+                else:
+                    lp = _loss(orc, Pp, c.model, rp, col, F, G)[0]
+                    lm = _loss(orc, Pm, c.model, rp, col, F, G)[0]
+                return (lp - lm) / (2 * st)
+            # Richardson: the O(step^2) error of the central difference cancels
+            fd = (4.0 * central(step / 2) - central(step)) / 3.0
             scale = max(abs(fd), 1e-3 * np.abs(g[:, :3]).max())
-            assert abs(g[i, a] - fd) <= 2e-5 * scale + 1e-9, (i, a, g[i, a], fd)
+            assert abs(g[i, a] - fd) <= 2e-5 * scale + 1e-9, (shape, i, a, g[i, a], fd)
             checked += 1
-    assert checked >= 60
+            film_z += int(c.model[i] == 1 and a == 2)
+    assert checked >= 120 and film_z >= 30
     assert np.all(g[:, 3] == 0.0)
+
+
+def test_film_frame_term_is_what_moves_a_flat_film_out_of_plane(orc):
+    # On a flat film every neighbour lies in the tangent plane, so moving a film
+    # particle out of the plane changes no in-plane coordinate and no weight to
+    # first order: its z-gradient comes only from the PCA normal turning the
+    # world-coordinate gradient outputs.  A loss on the Laplacian alone does
+    # not see that turn (the plane Laplacian ignores the frame's orientation),
+    # a loss on the gradient outputs does.
+    c = C.flat_film(0.05, 0.8, 0.015)
+    P = c.pos_h.astype(np.float64)
+    F = c.vp.astype(np.float64)
+    rp, col = orc.neighbours(P)
+    rng = np.random.default_rng(4)
+    G = rng.normal(size=(c.n, 4, 4))
+    G_lap = G.copy()
+    G_lap[:, :, :3] = 0.0
+    G_grad = G.copy()
+    G_grad[:, :, 3] = 0.0
+    assert np.all(orc.stencil_grad(P, c.model, rp, col, F, G_lap)[:, 2] == 0.0)
+    gz = orc.stencil_grad(P, c.model, rp, col, F, G_grad)[:, 2]
+    assert np.abs(gz).max() > 0.1 * np.abs(orc.stencil_grad(P, c.model, rp, col, F, G_grad)[:, :2]).max()
 
 
 def test_gradient_of_translation_invariant_loss_sums_to_zero(orc):
