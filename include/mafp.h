@@ -237,7 +237,9 @@ int mafp_build_stencils(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos
  *  - Every call shares the one array and resets the queue length itself, so
  *    calls whose work overlaps on the GPU (different streams, or host threads
  *    without ordering) race on it: serialise them.
- *  - Launch shapes are the defaults; device-side counters are not reported. */
+ *  - Launch shapes are the defaults; device-side counters are not reported,
+ *    and no error text is kept (there is no context to hold it): a failing
+ *    CUDA call shows only as MAFP_ECUDA. */
 #define MAFP_NOALLOC_MAX_PARTICLES (1 << 20)
 int mafp_build_stencils_noalloc(int64_t n, int32_t dtype, const mafp_params *params,
                                 const void *pos_h, const uint8_t *model, const void *frame,
@@ -277,14 +279,20 @@ int mafp_apply_ops_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const int64
                             const void *gout, void *gfields, void *stream);
 
 /* mafp_build_stencils_backward -- adjoint of (build_stencils, apply_ops) with
- * respect to the 3D particle positions, for a loss L that depends on
+ * respect to the particle positions, for a loss L that depends on
  * out = apply_ops(build_stencils(pos), fields) with gout = dL/dout:
  *   gpos[k] += sum over rows i and entries (i, j) of
  *              sum_op (sum_f gout[4i+f][op] fields[j][f]) d c_ij^op / d x_k,
  * recomputing the moment matrix and its Cholesky per particle (no stored
- * factors).  Neighbour sets, models and frames are held fixed.  Rows of 2D
- * particles contribute through their in-plane coordinates with the frame
- * held fixed.  gpos x4 [n] written (x, y, z, 0). */
+ * factors).  Neighbour sets and models are held fixed (piecewise constant).
+ * Rows of 2D particles: `frame` must be the particle's local PCA frame
+ * (Sec. 4.1.2) at these positions, as mafp_classify_pca writes it; its
+ * dependence on the positions is included through the normal w3 (first-order
+ * perturbation of the eigenvector of the scatter matrix, whose eigenvalues
+ * are recomputed as Rayleigh quotients in the given frame); turning (w1, w2)
+ * inside the plane changes no output and contributes nothing.  Rows whose
+ * moment matrix is rank deficient contribute nothing.
+ * gpos x4 [n] written (x, y, z, 0). */
 int mafp_build_stencils_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h,
                                  const uint8_t *model, const void *frame,
                                  const int64_t *row_ptr, const int32_t *col,

@@ -4,9 +4,13 @@
 applied operators out[i, f] = (d_x, d_y, d_z, Lap) of the four fields
 (Eq. GFDM_Definition with the stencils of Sec. 2.3).  Its backward runs the
 library's hand-written kernels: the exact transpose of apply_ops for the
-fields (scattered with atomic adds) and the stencil adjoint (moment matrix and Cholesky recomputed per
-particle) for the positions.  Neighbour sets, models and film tangent frames
-are inputs held fixed; the smoothing length column of pos_h gets no gradient.
+fields (scattered with atomic adds) and the stencil adjoint (moment matrix and
+Cholesky recomputed per particle) for the positions.  Neighbour sets and models
+are held fixed.  `frame` must be the tangent frame classify_pca computes from
+the same positions: the backward includes its dependence on the positions
+(through the PCA normal of each film row), so a caller that moves the particles
+recomputes it before the next forward.  The smoothing length column of pos_h
+gets no gradient.
 """
 from __future__ import annotations
 

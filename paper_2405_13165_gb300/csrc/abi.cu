@@ -48,16 +48,17 @@ int ghost_append(mafp_ctx *, int64_t, int64_t, int32_t, const mafp_state *, cons
                  int64_t, int64_t *, cudaStream_t);
 
 int sm_count() {
-  static int cached[64] = {0};
+  static int cached[64] = {0};   // per device; read and written atomically
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (!cached[dev]) {
-    int v = 0;
+  int v = __atomic_load_n(&cached[dev], __ATOMIC_ACQUIRE);
+  if (!v) {
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    cached[dev] = v > 0 ? v : 1;
+    v = v > 0 ? v : 1;
+    __atomic_store_n(&cached[dev], v, __ATOMIC_RELEASE);
   }
-  return cached[dev];
+  return v;
 }
 }  // namespace mafp
 
@@ -124,11 +125,7 @@ int mafp_create(mafp_ctx **out, const mafp_params *params, int64_t cap_particles
   mafp_ctx *ctx = (mafp_ctx *)calloc(1, sizeof(mafp_ctx));
   if (!ctx) return MAFP_ECUDA;
   if (params) ctx->prm = *params; else mafp_default_params(&ctx->prm);
-  ctx->tune.stencil3d_group = 32;
-  ctx->tune.stencil2d_group = 8;
-  ctx->tune.apply_group = 8;
-  ctx->tune.grad3d_group = 4;
-  ctx->tune.grad2d_group = 2;
+  default_tuning(&ctx->tune);
   ctx->cap_particles = cap_particles;
   ctx->cap_cells = cap_cells;
   cudaGetDevice(&ctx->device);

@@ -200,6 +200,35 @@ inline int grid_for(int64_t work, int per_block, int max_blocks = 1 << 20) {
 
 int sm_count();
 
+// Launch shapes of a new context (and of the context-free entry point).
+inline void default_tuning(mafp_tuning *t) {
+  t->stencil3d_group = 32;
+  t->stencil2d_group = 8;
+  t->apply_group = 8;
+  t->grad3d_group = 4;
+  t->grad2d_group = 2;
+}
+
+// Name of a kernel instance for the timing record: built once (function-local
+// statics are initialised thread-safely) and never written again, so launches
+// from several host threads or devices share it safely.
+struct KernelName {
+  char s[96];
+  template <typename... A>
+  explicit KernelName(const char *fmt, A... a) {
+    snprintf(s, sizeof(s), fmt, a...);
+  }
+};
+
+// One bit per device (devices 0..63): set once a per-device, per-function
+// setting (such as a dynamic shared-memory limit) has been applied there.
+// Returns true when the caller still has to apply it on `dev`.
+inline bool first_on_device(unsigned long long *mask, int dev) {
+  if (dev < 0 || dev >= 64) return true;
+  const unsigned long long bit = 1ull << dev;
+  return (__atomic_fetch_or(mask, bit, __ATOMIC_ACQ_REL) & bit) == 0;
+}
+
 constexpr int kProfCap = 4096;
 
 // Bracket one kernel launch with CUDA events on its stream when profiling is on.

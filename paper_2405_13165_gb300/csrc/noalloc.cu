@@ -72,11 +72,7 @@ extern "C" int mafp_build_stencils_noalloc(int64_t n, int32_t dtype, const mafp_
   mafp_ctx c;
   memset(&c, 0, sizeof(c));
   if (params) c.prm = *params; else mafp_default_params(&c.prm);
-  c.tune.stencil3d_group = 32;
-  c.tune.stencil2d_group = 8;
-  c.tune.apply_group = 8;
-  c.tune.grad3d_group = 4;
-  c.tune.grad2d_group = 2;
+  default_tuning(&c.tune);
   c.cap_particles = kNoAllocMaxParticles;
   c.device = dev;
   c.fallback = scr->queue;

@@ -322,18 +322,16 @@ static void launch_stencil(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void 
                            const int32_t *col, void *coef, uint8_t *status, float *cond,
                            const StParams<C> &sp) {
   using V = vec4_t<TS>;
-  static char name[96];
-  snprintf(name, sizeof(name), "k_stencil<%s,M=%d,G=%d,%s>", sizeof(TS) == 4 ? "f32" : "f64",
-           M, G, REFINE ? "refined" : "plain");
+  static const KernelName name("k_stencil<%s,M=%d,G=%d,%s>", sizeof(TS) == 4 ? "f32" : "f64",
+                               M, G, REFINE ? "refined" : "plain");
   const int blocks = grid_for(n * G, kStThreads, sm_count() * 64);
   constexpr int smem = StCache<C, M, G>::SMEM;
-  static bool attr_set = false;
-  if (!attr_set && smem > 48 * 1024) {
+  // the dynamic shared-memory limit is a per-device setting of the function
+  static unsigned long long attr_devices = 0;
+  if (smem > 48 * 1024 && first_on_device(&attr_devices, ctx->device))
     cudaFuncSetAttribute(k_stencil<TS, C, M, G, REFINE, QUEUE>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr_set = true;
-  }
-  MAFP_TIMED(ctx, s, name,
+  MAFP_TIMED(ctx, s, name.s,
              k_stencil<TS, C, M, G, REFINE, QUEUE><<<blocks, kStThreads, smem, s>>>(
                  n, (const V *)pos_h, model, (const V *)frame, rp, col, (V *)coef, status, cond,
                  sp, ctx->d_status, ctx->fallback));

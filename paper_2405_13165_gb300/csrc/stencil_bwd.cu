@@ -9,9 +9,20 @@
 //   wbar_j = sum_k (gbar_jk - t_jk) s_jk,
 //   pbar_j = w_j sum_k (gbar_jk lambda_k - s_jk mu_k - t_jk lambda_k),
 // then through p(q) and W(|q|) to q_j = (x_j - x_i)/h_i, scattered to x_j and
-// x_i (atomic adds).  Film rows use the tangent frame of `frame` held fixed.
-// The unscaled right-hand sides of the forward kernel are used; the 1/h and
-// 1/h^2 output factors are folded into gbar.
+// x_i (atomic adds).  The unscaled right-hand sides of the forward kernel are
+// used; the 1/h and 1/h^2 output factors are folded into gbar.
+//
+// Film rows: the tangent frame (t1, t2, n = w3) is the local PCA of Sec. 4.1.2
+// over the same-model part of S_i, so it moves with the positions too.  The
+// outputs do not change when (t1, t2) turn inside the plane; only n matters.
+// With tbar_k = dL/dt_k at fixed n (through xi = d.t1/h, eta = d.t2/h and the
+// world-coordinate gradient c^xi t1 + c^eta t2), turning the frame with n and
+// the first-order perturbation of the eigenvector w3 of the scatter matrix
+// Ps = sum_j z_j z_j^T (z_j = y_j - y_c, y_j = (x_j - x_i)/h) give
+//   dL/dy_j = sum_k beta_k (t_k (n.z_j) + n (t_k.z_j)),  beta_k = (tbar_k.n)/(l_k - l3),
+// with l_k = t_k^T Ps t_k (Rayleigh quotients in the given frame).  The gradient
+// pass sums n.tbar_k; a third pass over the row sums y_j and y_j y_j^T and a
+// fourth scatters the term.
 #include "internal.cuh"
 #include "stencil_common.cuh"
 
@@ -49,14 +60,14 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
   const V xi = ld4(pos + i);
   const uint8_t mi = model[i];
   const C hinv = C(1) / C(xi.w);
-  C t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0};
+  C t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0}, nv[3] = {0, 0, 0};
   if constexpr (M == 6) {
     const V f1 = ld4(frame + 2 * i), f3 = ld4(frame + 2 * i + 1);
     t1[0] = C(f1.x); t1[1] = C(f1.y); t1[2] = C(f1.z);
-    const C n0 = C(f3.x), n1 = C(f3.y), n2 = C(f3.z);
-    t2[0] = n1 * t1[2] - n2 * t1[1];
-    t2[1] = n2 * t1[0] - n0 * t1[2];
-    t2[2] = n0 * t1[1] - n1 * t1[0];
+    nv[0] = C(f3.x); nv[1] = C(f3.y); nv[2] = C(f3.z);
+    t2[0] = nv[1] * t1[2] - nv[2] * t1[1];
+    t2[1] = nv[2] * t1[0] - nv[0] * t1[2];
+    t2[2] = nv[0] * t1[1] - nv[1] * t1[0];
   }
   const long long b = row_ptr[i], e1 = row_ptr[i + 1];
   // per-operator output scale of the forward kernel: gradient 1/h, Laplacian 1/h^2
@@ -66,9 +77,9 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
 #pragma unroll
   for (int f = 0; f < 4; ++f) go[f] = ld4(gout + 4 * i + f);
   // gbar (scaled) of one neighbour, in the basis' operator order
-  auto gbar = [&](const V &fj, C (&gb)[NR]) {
+  auto gbar = [&](const V &fj, C (&gb)[NR], C (&g4)[4]) {
     const C du[4] = {C(fj.x) - C(fi.x), C(fj.y) - C(fi.y), C(fj.z) - C(fi.z), C(fj.w) - C(fi.w)};
-    C g4[4] = {0, 0, 0, 0};
+    g4[0] = g4[1] = g4[2] = g4[3] = C(0);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       g4[0] += C(go[f].x) * du[f];
@@ -190,6 +201,7 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
   // ---- pass 2: wbar, pbar -> dL/dx_j (scattered) and -sum for x_i
   const C a2 = C(-2) * sp.alpha * sp.inv_den;  // W'(s)/s = a2 exp(-alpha s^2)
   C acc_i[3] = {0, 0, 0};
+  C tn1 = 0, tn2 = 0;   // film rows: n . dL/dt1 and n . dL/dt2 at fixed n
   for (long long e0 = b + lane; e0 < e1; e0 += kGradGatherC * G) {
     V xs[kGradGatherC], fs[kGradGatherC];
     int js[kGradGatherC];
@@ -200,15 +212,15 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
     const int j = js[u];
     if (!oks[u] || j == i) continue;
     const V xj = xs[u];
-    C p[M], gb[NR];
+    C p[M], gb[NR], g4[4];
     const C w = basis_at<M, C>(xi, xj, hinv, t1, t2, sp, p);
-    gbar(fs[u], gb);
+    gbar(fs[u], gb, g4);
     const C dx = C(xj.x) - C(xi.x), dy = C(xj.y) - C(xi.y), dz = C(xj.z) - C(xi.z);
     const C s2 = ((dx * dx + dy * dy) + dz * dz) * (hinv * hinv);
     const C dws = s2 <= C(1) ? a2 * exp(-sp.alpha * s2) : C(0);
     // pbar = w sum_k ((gbar_k - t_k) lambda_k - s_k mu_k); pbar_0 is not needed
     // (d p_0 / d q = 0) and the factor w is applied to the gradient below
-    C wbar = 0, pbar[M];
+    C wbar = 0, pbar[M], s01[2] = {0, 0};
 #pragma unroll
     for (int r = 0; r < M; ++r) pbar[r] = 0;
 #pragma unroll
@@ -219,6 +231,7 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
         s += p[r] * lam[k][r];
         t += p[r] * mu[k][r];
       }
+      if (k < 2) s01[k] = s;
       const C a = gb[k] - t;
       wbar += a * s;
 #pragma unroll
@@ -241,10 +254,67 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
       d[0] = (xb * t1[0] + eb * t2[0]) * hinv + wq * dx * hinv * hinv;
       d[1] = (xb * t1[1] + eb * t2[1]) * hinv + wq * dy * hinv * hinv;
       d[2] = (xb * t1[2] + eb * t2[2]) * hinv + wq * dz * hinv * hinv;
+      // the frame through xi, eta and through c^xi t1 + c^eta t2 (c^xi = w s_0 / h);
+      // only the normal components of dL/dt_k are needed
+      const C dn = dx * nv[0] + dy * nv[1] + dz * nv[2];
+      const C gn = g4[0] * nv[0] + g4[1] * nv[1] + g4[2] * nv[2];
+      tn1 += (xb * dn + w * s01[0] * gn) * hinv;
+      tn2 += (eb * dn + w * s01[1] * gn) * hinv;
     }
     add_xyz<TS>(gpos + 4 * (int64_t)j, TS(d[0]), TS(d[1]), TS(d[2]));
 #pragma unroll
     for (int a = 0; a < 3; ++a) acc_i[a] -= d[a];
+    }
+  }
+  if constexpr (M == 6) {
+    // ---- pass 3 (film rows): the PCA frame's dependence on the positions.
+    // First sum_j y_j and sum_j y_j y_j^T (xx, yy, zz, xy, xz, yz) over the
+    // same-model part of the row (a separate pass keeps these sums out of the
+    // registers of the two heavy passes), then scatter the frame term.
+    tn1 = group_sum<G>(tn1);
+    tn2 = group_sum<G>(tn2);
+    C sy[3] = {0, 0, 0}, syy[6] = {0, 0, 0, 0, 0, 0};
+    for (long long e = b + lane; e < e1; e += G) {
+      const int j = col[e];
+      if (j == i || model[j] != mi) continue;
+      const V xj = ld4(pos + j);
+      const C y0 = (C(xj.x) - C(xi.x)) * hinv, y1 = (C(xj.y) - C(xi.y)) * hinv,
+              y2 = (C(xj.z) - C(xi.z)) * hinv;
+      sy[0] += y0; sy[1] += y1; sy[2] += y2;
+      syy[0] += y0 * y0; syy[1] += y1 * y1; syy[2] += y2 * y2;
+      syy[3] += y0 * y1; syy[4] += y0 * y2; syy[5] += y1 * y2;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sy[a] = group_sum<G>(sy[a]);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) syy[a] = group_sum<G>(syy[a]);
+    const C inv_m = C(1) / C(cnt);
+    const C yc[3] = {sy[0] * inv_m, sy[1] * inv_m, sy[2] * inv_m};
+    // Ps = sum_j y_j y_j^T - m y_c y_c^T, quadratic form v^T Ps v
+    auto quad = [&](const C (&v)[3]) {
+      const C vy = v[0] * sy[0] + v[1] * sy[1] + v[2] * sy[2];
+      const C q = v[0] * v[0] * syy[0] + v[1] * v[1] * syy[1] + v[2] * v[2] * syy[2] +
+                  C(2) * (v[0] * v[1] * syy[3] + v[0] * v[2] * syy[4] + v[1] * v[2] * syy[5]);
+      return q - vy * vy * inv_m;
+    };
+    const C l3 = quad(nv), g1 = quad(t1) - l3, g2 = quad(t2) - l3;
+    const C be1 = g1 > C(0) ? tn1 / g1 : C(0);
+    const C be2 = g2 > C(0) ? tn2 / g2 : C(0);
+    for (long long e = b + lane; e < e1; e += G) {
+      const int j = col[e];
+      if (j == i || model[j] != mi) continue;
+      const V xj = ld4(pos + j);
+      const C z0 = (C(xj.x) - C(xi.x)) * hinv - yc[0], z1 = (C(xj.y) - C(xi.y)) * hinv - yc[1],
+              z2 = (C(xj.z) - C(xi.z)) * hinv - yc[2];
+      const C nz = nv[0] * z0 + nv[1] * z1 + nv[2] * z2;
+      const C u1 = be1 * (t1[0] * z0 + t1[1] * z1 + t1[2] * z2);
+      const C u2 = be2 * (t2[0] * z0 + t2[1] * z1 + t2[2] * z2);
+      C d[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) d[a] = ((be1 * t1[a] + be2 * t2[a]) * nz + nv[a] * (u1 + u2)) * hinv;
+      add_xyz<TS>(gpos + 4 * (int64_t)j, TS(d[0]), TS(d[1]), TS(d[2]));
+#pragma unroll
+      for (int a = 0; a < 3; ++a) acc_i[a] -= d[a];
     }
   }
 #pragma unroll
@@ -302,10 +372,9 @@ static void launch_grad_g(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void *
                           const int32_t *col, const void *fields, const void *gout, void *gpos,
                           const StParams<C> &sp) {
   using V = vec4_t<TS>;
-  static char name[64];
-  snprintf(name, sizeof(name), "k_stencil_grad<%s,M=%d,G=%d>", sizeof(TS) == 4 ? "f32" : "f64",
-           M, G);
-  MAFP_TIMED(ctx, s, name,
+  static const KernelName name("k_stencil_grad<%s,M=%d,G=%d>", sizeof(TS) == 4 ? "f32" : "f64",
+                               M, G);
+  MAFP_TIMED(ctx, s, name.s,
              (k_stencil_grad<TS, C, M, G, QUEUE><<<grid_for(n * G, kStThreads, sm_count() * 64),
                                                    kStThreads, 0, s>>>(
                  n, (const V *)pos_h, model, (const V *)frame, rp, col, (const V *)fields,

@@ -1,7 +1,9 @@
 """GPU gradients through the C ABI: the transpose of apply_ops (fields) and the
 stencil adjoint (positions), against the FP64 oracle gradient (itself pinned by
-central finite differences) and, in FP64, against torch's own finite-difference
-gradcheck of the GPU forward."""
+central finite differences) and, in FP64, against finite differences of the
+GPU forward.  Film rows take their tangent frame from the local PCA of the
+positions, so every forward evaluated at moved positions recomputes the frame
+(classify) first; flat, tilted and curved films are covered."""
 import numpy as np
 import pytest
 
@@ -17,6 +19,7 @@ import oracle as O  # noqa: E402
 from paper_2405_13165_gb300 import mafp as M  # noqa: E402
 from paper_2405_13165_gb300.autograd import gfdm_operators  # noqa: E402
 from parity_util import run_gpu  # noqa: E402
+from grad_shapes import SHAPES, shape  # noqa: E402
 
 
 def _setup(c, dtype):
@@ -26,10 +29,26 @@ def _setup(c, dtype):
     return ctx, d, rp, col, pipe.frame[:n].clone()
 
 
+def frame_of(ctx, d, pos, rp, col, dtype):
+    """The tangent frames classify computes at positions `pos` (neighbour sets
+    held fixed), as a forward at moved positions needs them."""
+    n = pos.shape[0]
+    rd = M.real_dtype(dtype)
+    u8 = lambda: torch.empty(n, dtype=torch.uint8, device="cuda")
+    frame = torch.empty(n, 8, dtype=rd, device="cuda")
+    M.classify_pca(ctx, pos.contiguous(), d["model"], d["ptype"], d["normal"], d["vol"], d["h3d"],
+                   d["user"], d["last"], rp, col, u8(), u8(),
+                   torch.empty(n, 4, dtype=rd, device="cuda"), frame,
+                   torch.empty(n, dtype=rd, device="cuda"), None, dtype)
+    return frame
+
+
+@pytest.mark.parametrize("shape_name", SHAPES)
 @pytest.mark.parametrize("dtype", [M.F32_REFINED, M.F64])
 @pytest.mark.parametrize("loss", ["laplacian", "random"])
-def test_position_gradient_matches_oracle(dtype, loss):
-    c = C.cube_on_sheet(0.04, cube=0.32, sheet=1.0)
+def test_position_gradient_matches_oracle(dtype, loss, shape_name):
+    c = (C.cube_on_sheet(0.04, cube=0.32, sheet=1.0) if shape_name == "flat"
+         else shape(shape_name)[0])
     ctx, d, rp, col, frame = _setup(c, dtype)
     pos = d["pos_h"].clone().requires_grad_(True)
     fields = d["fields"].clone().requires_grad_(True)
@@ -65,21 +84,76 @@ def test_position_gradient_matches_oracle(dtype, loss):
     ctx.close()
 
 
-def test_gradcheck_fp64_tiny_cloud():
-    # FP64 forward and hand-written backward agree with torch's finite differences
+@pytest.mark.parametrize("shape_name", ["flat", "tilted"])
+def test_gradcheck_fp64_tiny_cloud(shape_name):
+    # FP64 forward and hand-written backward agree with torch's finite
+    # differences; the forward recomputes the film frames from the positions
     c = C.cube_on_sheet(0.1, cube=0.5, sheet=1.0)        # 125 + 75 particles
+    if shape_name == "tilted":
+        c = C.rotated(c, (1.0, 0.4, 0.2), 0.6)
     ctx, d, rp, col, frame = _setup(c, M.F64)
     pos = d["pos_h"].clone().requires_grad_(True)
     fields = d["fields"].clone().requires_grad_(True)
 
     def f(p, u):
         # only x, y, z carry gradients; h enters as a constant
-        full = torch.cat([p, d["pos_h"][:, 3:]], 1)
-        return gfdm_operators(ctx, full.contiguous(), u, rp, col, d["model"], frame, M.F64)
+        full = torch.cat([p, d["pos_h"][:, 3:]], 1).contiguous()
+        fr = frame_of(ctx, d, full.detach(), rp, col, M.F64)
+        return gfdm_operators(ctx, full, u, rp, col, d["model"], fr, M.F64)
 
     xyz = pos[:, :3].detach().clone().requires_grad_(True)
     assert torch.autograd.gradcheck(f, (xyz, fields), eps=1e-7, atol=1e-6, rtol=1e-5,
                                     nondet_tol=1e-9, fast_mode=True)
+    ctx.close()
+
+
+@pytest.mark.parametrize("shape_name", SHAPES)
+def test_fp64_film_gradient_matches_central_differences(shape_name):
+    """Every coordinate of film particles, FP64 GPU adjoint against central
+    differences of the FP64 GPU forward (frames recomputed at every point)."""
+    c, dx = shape(shape_name)
+    ctx, d, rp, col, frame = _setup(c, M.F64)
+    n = c.n
+    rng = np.random.default_rng(8)
+    G = torch.tensor(rng.normal(size=(n, 4, 4)), dtype=torch.float64, device="cuda")
+    coef = torch.empty(col.numel(), 4, dtype=torch.float64, device="cuda")
+    status = torch.empty(n, dtype=torch.uint8, device="cuda")
+    cond = torch.empty(n, dtype=torch.float32, device="cuda")
+    out = torch.empty(n, 4, 4, dtype=torch.float64, device="cuda")
+
+    def loss(pos):
+        fr = frame_of(ctx, d, pos, rp, col, M.F64)
+        M.build_stencils(ctx, pos, d["model"], fr, rp, col, coef, status, cond, M.F64)
+        M.apply_ops(ctx, rp, col, coef, d["fields"], out, M.F64)
+        return float((out * G).sum().item())
+
+    pos = d["pos_h"].clone()
+    gpos = torch.empty_like(pos)
+    M.build_stencils_backward(ctx, pos, d["model"], frame, rp, col, d["fields"], G, gpos, M.F64)
+    g = gpos.cpu().numpy()
+    P = c.pos_h.astype(np.float64)
+    rpn, coln = rp.cpu().numpy(), col.cpu().numpy()
+    step = 1e-4 * dx
+    film = np.nonzero(c.model == 1)[0]
+    checked = 0
+    for k in rng.permutation(film):
+        r = coln[rpn[k]:rpn[k + 1]]
+        dist = np.linalg.norm(P[r, :3] - P[k, :3], axis=1)
+        if np.any(np.abs(dist - 0.5 * (P[r, 3] + P[k, 3])) <= 10 * step):
+            continue
+        for a in (0, 1, 2):
+            def central(st):
+                pp, pm = pos.clone(), pos.clone()
+                pp[k, a] += st
+                pm[k, a] -= st
+                return (loss(pp) - loss(pm)) / (2 * st)
+            fd = (4.0 * central(step / 2) - central(step)) / 3.0
+            scale = max(abs(fd), 1e-3 * np.abs(g[:, :3]).max())
+            assert abs(g[k, a] - fd) <= 1e-5 * scale + 1e-9, (shape_name, k, a, g[k, a], fd)
+            checked += 1
+        if checked >= 45:
+            break
+    assert checked >= 45
     ctx.close()
 
 

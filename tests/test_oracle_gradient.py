@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2405_13165_gb300 import clouds as C
+from grad_shapes import SHAPES, shape as _shape
 
 
 def _loss(orc, P, model, rp, col, F, G):
@@ -21,20 +22,7 @@ def _safe_coords(P, rp, col, i, step):
     return np.all(np.abs(d - P[i, 3]) > 10 * step)
 
 
-def _shape(name):
-    """Flat, tilted and curved films (the last two with film rows whose
-    neighbours lie off their tangent plane), with a 3D cube where there is one."""
-    if name == "flat":
-        return C.cube_on_sheet(0.05, cube=0.4, sheet=1.0), 0.05      # 512 + 384 particles
-    if name == "tilted":
-        return C.rotated(C.cube_on_sheet(0.05, cube=0.4, sheet=1.0), (1.0, 0.4, 0.2), 0.6), 0.05
-    cap = C.curved_film(0.05, 0.55, 0.7)
-    cube = C.cube_on_sheet(0.05, cube=0.25, sheet=0.35)
-    cube.pos_h[:, 2] += 0.5    # lifted clear of the cap
-    return C.concat([cap, cube]), 0.05
-
-
-@pytest.mark.parametrize("shape", ["flat", "tilted", "curved"])
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("loss", ["laplacian", "random"])
 def test_gradient_matches_central_differences(orc, loss, shape):
     c, dx = _shape(shape)
