@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the compact record of the 256-cloud batch in the default run")
     ap.add_argument("--workload", default="jet", choices=["jet", "batched", "tray"],
                     help="jet: the 1M jet-on-plate step (default); batched: 256 independent "
                          "cube-on-sheet clouds, forward pass replayed from a CUDA graph; "
@@ -140,12 +142,11 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle
 def cpu_oracle_sample(cloud, m: int):
-    """The FP64 oracle on the step's stages: neighbours, detection, smoothing,
-    remap, stencils, apply and apply transpose on the first m particles (cell
-    order; m = the whole cloud by default), and the single-threaded stencil
-    adjoint on a seeded 5 % of the rows (the oracle skips rows whose output
-    gradient is zero), its time scaled by 20.  Returns (seconds for the whole
-    sample, threads, description, particles)."""
+    """The FP64 oracle on the step's stages over the first m particles (cell
+    order; m = the whole cloud by default): neighbours, detection, smoothing,
+    remap, stencils, apply, apply transpose and the stencil adjoint, all rows,
+    OpenMP over particles on every host core.  Returns (seconds, threads,
+    description, particles, the oracle's applied outputs)."""
     import oracle
     sub = cloud.take(np.arange(min(m, cloud.n)))
     t0 = time.perf_counter()
@@ -157,19 +158,31 @@ def cpu_oracle_sample(cloud, m: int):
     coef, status, cond = oracle.stencils(sub.pos_h, sub.model, rp, col)
     out = oracle.apply(rp, col, coef, sub.vp)
     oracle.apply_T(rp, col, coef, out)
-    t1 = time.perf_counter()
-    G = np.zeros_like(out)
-    rows = np.random.default_rng(5).random(sub.n) < 0.05
-    G[rows] = out[rows]
-    oracle.stencil_grad(sub.pos_h, sub.model, rp, col, sub.vp, G)
-    t2 = time.perf_counter()
-    dt = (t1 - t0) + (t2 - t1) / 0.05
+    oracle.stencil_grad(sub.pos_h, sub.model, rp, col, sub.vp, out)
+    dt = time.perf_counter() - t0
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     desc = (f"first {sub.n} particles (cell order) of the same cloud: oracle neighbours, "
-            f"detection, smoothing, remap, stencils, apply, apply transpose in FP64 "
-            f"({t1 - t0:.1f} s, OpenMP); stencil adjoint single-threaded on a seeded 5 % of "
-            f"the rows ({t2 - t1:.1f} s, scaled x20)")
-    return dt, threads, desc, sub.n
+            f"detection, smoothing, remap, stencils, apply, apply transpose and stencil "
+            f"adjoint in FP64 on all rows, OpenMP over particles ({threads} threads)")
+    return dt, threads, desc, sub.n, out
+
+
+COLUMNS = [f"{f}.{op}" for f in ("u", "v", "w", "p") for op in ("dx", "dy", "dz", "lap")]
+
+
+def error_per_output(a, b):
+    """Per output (field . operator) error of `a` against the FP64 oracle
+    outputs `b`: normwise max |a - b| / max |b| over the particles, and the
+    p99 of the componentwise |a - b| / max(|b|, 1e-3 max |b|)."""
+    a = np.asarray(a, np.float64).reshape(-1, 16)
+    b = np.asarray(b, np.float64).reshape(-1, 16)
+    scale = np.abs(b).max(0)
+    diff = np.abs(a - b)
+    nw = diff.max(0) / np.where(scale > 0, scale, 1.0)
+    comp = diff / np.maximum(np.abs(b), 1e-3 * scale)
+    p99 = np.percentile(comp, 99, axis=0)
+    return {c: {"normwise": float(f"{nw[k]:.3e}"), "p99": float(f"{p99[k]:.3e}")}
+            for k, c in enumerate(COLUMNS)}
 
 
 def gen_cloud(n):
@@ -434,15 +447,23 @@ def bench_gpu(args):
             torch.cuda.synchronize()
             t64 += e0.elapsed_time(e1)
         t64 /= k64
-        e0.record(stream)
-        pipe.neighbours(d)
-        pipe.classify(d)
-        pipe.stencils(d)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t32 = e0.elapsed_time(e1)
+        pipe64.apply(d64)
+        out64 = pipe64.out[:n].cpu().numpy()
+        t32 = 0.0
+        for _ in range(k64):
+            flush.fill_(1)
+            e0.record(stream)
+            pipe.neighbours(d)
+            pipe.classify(d)
+            pipe.stencils(d)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t32 += e0.elapsed_time(e1)
+        t32 /= k64
+        pipe.apply(d)
+        out32 = pipe.out[:n].cpu().numpy()
         fp64 = {"build_ms_fp64": round(t64, 3), "build_ms_fp32_refined": round(t32, 3),
-                "speedup": round(t64 / t32, 2),
+                "repeats": k64, "speedup": round(t64 / t32, 2),
                 "build_particles_per_s_fp32_refined": round(n / (t32 * 1e-3), 1),
                 "build_particles_per_s_fp64": round(n / (t64 * 1e-3), 1)}
         del pipe64, d64
@@ -487,9 +508,25 @@ def bench_gpu(args):
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, thr, desc, m = cpu_oracle_sample(cloud, args.cpu_sample)
+        dt, thr, desc, m, o_out = cpu_oracle_sample(cloud, args.cpu_sample)
         cpu = {"value": round(m / dt, 1), "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": desc, "seconds": round(dt, 2)}
+        if fp64 is not None and m == n:
+            # error per output of both GPU paths against the FP64 oracle on the whole cloud
+            e32, e64 = error_per_output(out32, o_out), error_per_output(out64, o_out)
+            fp64["err_per_output"] = {
+                "fp32_refined": e32, "fp64": e64,
+                "fp32_refined_max_normwise": max(v["normwise"] for v in e32.values()),
+                "fp32_refined_max_p99": max(v["p99"] for v in e32.values()),
+                "fp64_max_normwise": max(v["normwise"] for v in e64.values()),
+                "bar": {"fp32_refined": 1e-4, "fp64": 1e-10},
+                "measure": "per field.operator over all particles: normwise max|a-b|/max|b|, "
+                           "p99 of |a-b|/max(|b|, 1e-3 max|b|); b = FP64 oracle"}
+
+    # ---- the batched workload (256 independent clouds), compact record
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = run_batched(args, dev, 1, 0, compact=True)
 
     if rank == 0:
         line = {
@@ -513,6 +550,7 @@ def bench_gpu(args):
             "kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
                             for kk, vv in v.items()} for k, v in kernels.items()},
             "fp64_vs_fp32": fp64,
+            "batched": batched,
             "tuning": tuned,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -531,17 +569,8 @@ def bench_gpu(args):
 
 
 def bench_batched(args):
-    """256 independent clouds in one batch (about 12M particles): neighbours,
-    detection, stencils and apply over the whole batch, one launch per stage,
-    the pass captured once in a CUDA graph and replayed.  Timed both eagerly
-    and by graph replay; L2 flushed before every timed pass."""
+    """The batched workload alone (--workload batched), one JSON line."""
     import torch
-
-    from paper_2405_13165_gb300 import autotune, clouds as C, mafp as M
-    from paper_2405_13165_gb300.pipeline import Pipeline, cloud_to_device
-
-    from paper_2405_13165_gb300 import shard
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
@@ -549,6 +578,29 @@ def bench_batched(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    line = run_batched(args, dev, world, rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_batched(args, dev, world, rank, compact=False):
+    """256 independent clouds in one batch (about 12M particles): neighbours,
+    detection, stencils and apply over the whole batch, one launch per stage,
+    the pass captured once in a CUDA graph and replayed.  Timed both eagerly
+    and by graph replay, and the same pass eagerly in FP64 (the plain FP64 GPU
+    path); L2 flushed before every timed pass.  compact: a short record for
+    the default run's line instead of a full line."""
+    import torch
+
+    from paper_2405_13165_gb300 import autotune, clouds as C, mafp as M
+    from paper_2405_13165_gb300.pipeline import Pipeline, cloud_to_device
+
+    from paper_2405_13165_gb300 import shard
+
     # whole clouds per rank (no collective on the data path), longest first
     parts = shard.assign_clouds(C.batched_sizes()[0], world)
     cloud, off = C.config_batched(select=parts[rank])
@@ -583,10 +635,10 @@ def bench_batched(args):
     ctx.profile(False)
     launches = sum(v[0] for v in prof.values())
 
-    def timed(run):
+    def timed(run, steps):
         tot = 0.0
         with torch.cuda.stream(s):
-            for _ in range(args.steps):
+            for _ in range(steps):
                 flush.fill_(1)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(s)
@@ -594,18 +646,31 @@ def bench_batched(args):
                 e1.record(s)
                 s.synchronize()
                 tot += e0.elapsed_time(e1)
-        return tot / args.steps
+        return tot / steps
 
     sampler = ClockSampler(dev.index)
     sampler.start()
     time.sleep(0.3)
-    ms_eager = max_over_ranks(timed(lambda: pipe.step(d, stream=s)), dev, world)
-    ms_graph = max_over_ranks(timed(graph.replay), dev, world)
+    ms_eager = max_over_ranks(timed(lambda: pipe.step(d, stream=s), args.steps), dev, world)
+    ms_graph = max_over_ranks(timed(graph.replay, args.steps), dev, world)
     clocks = sampler.stop()
     n_all = int(sum_over_ranks(n, dev, world))
     st = ctx.status()
     if st["code"] != 0:
         raise RuntimeError(f"device status after the batched passes: {st}")
+    del graph
+    # the same batched pass in FP64 throughout (the plain FP64 GPU path)
+    del pipe
+    d64 = cloud_to_device(cloud, M.F64, dev, cloud_offset=off)
+    pipe64 = Pipeline(ctx, n, nnz + 1024, M.F64, dev)
+    with torch.cuda.stream(s):
+        pipe64.step(d64, stream=s)
+    s.synchronize()
+    ms_fp64 = max_over_ranks(timed(lambda: pipe64.step(d64, stream=s), 2), dev, world)
+    st64 = ctx.status()
+    if st64["code"] != 0:
+        raise RuntimeError(f"device status after the FP64 batched passes: {st64}")
+    del pipe64, d64
     hit = [v for k, v in prof.items() if k.startswith("k_apply<G=")]
     peaks = {}
     try:
@@ -624,6 +689,17 @@ def bench_batched(args):
                 "traffic": None, "launch_ms": round(ms, 4),
                 "peak_source": "of measured" if "hbm_gbs" in peaks else "of fallback"}
     sizes = np.diff(off)
+    workload = (f"batch of {nb} independent cube-on-sheet clouds, sizes log-uniform 2k-200k, "
+                f"film fraction U[0.1, 0.9], dx = 0.02 m")
+    fp64 = {"ms_per_pass_fp64": round(ms_fp64, 3), "speedup_graph_fp32_refined_vs_fp64":
+            round(ms_fp64 / ms_graph, 2), "repeats": 2}
+    if compact:
+        return {"workload": workload, "n_particles": n, "nnz": nnz, "clouds": nb,
+                "ms_per_pass_graph": round(ms_graph, 3), "ms_per_pass_eager": round(ms_eager, 3),
+                "particles_per_s": round(n / (ms_graph * 1e-3), 1), "fp64": fp64,
+                "apply_roofline": roof, "clocks": clocks, "steps": args.steps,
+                "pass": "neighbours, detection, stencils, apply over all clouds, one launch per "
+                        "stage, CUDA graph replay; L2 flushed before every timed pass"}
     line = {
         "metric": "particles/s for neighbour+PCA+stencil build+apply over a batch of clouds",
         "value": round(n_all / (ms_graph * 1e-3), 1), "unit": UNIT, "n_gpus": world,
@@ -631,8 +707,7 @@ def bench_batched(args):
         "ms_per_step_eager": round(ms_eager, 4), "higher_is_better": True,
         "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded cube-on-sheet clouds)",
-        "config": {"workload": f"batch of {nb} independent cube-on-sheet clouds, sizes log-uniform "
-                               f"2k-200k, film fraction U[0.1, 0.9], dx = 0.02 m",
+        "config": {"workload": workload,
                    "n_particles": n_all, "n_particles_rank0": n, "nnz_rank0": nnz,
                    "clouds": len(C.batched_sizes()[0]), "clouds_rank0": nb,
                    "smallest": int(sizes.min()),
@@ -641,6 +716,7 @@ def bench_batched(args):
                    "l2": "flushed (256 MB write) before every timed pass",
                    "parallelism": (f"{world} ranks, whole clouds per rank (longest first)"
                                    if world > 1 else "single GPU")},
+        "fp64": fp64,
         "roofline": roof, "tuning": tuned, "clocks": clocks,
         "gpu_launches": int(launches * args.steps),
         "kernel_profile_top": [{"kernel": k, "launches": v[0],
@@ -649,12 +725,7 @@ def bench_batched(args):
         "device_status": {k: st[k] for k in ("code", "n_fp64_stencil", "n_fp64_eigen",
                                              "n_deficient", "n_near", "cells_identity")},
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        dist.destroy_process_group()
+    return line
 
 
 def bench_tray(args):
@@ -773,7 +844,7 @@ def bench_reference(args):
     oracle.build()
     times = []
     for _ in range(args.steps):
-        dt, thr, desc, mm = cpu_oracle_sample(cloud, m)
+        dt, thr, desc, mm, _ = cpu_oracle_sample(cloud, m)
         times.append(dt)
     ms = 1e3 * statistics.mean(times)
     value = mm / (ms * 1e-3)
@@ -782,6 +853,7 @@ def bench_reference(args):
             "ms_per_step": round(ms, 2), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded jet-on-plate cloud)",
             "config": {"workload": WORKLOAD, "n_particles": cloud.n, "sample_particles": mm},
+            "timed_region_s": round(sum(times), 2),
             "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "kind": "oracle",
                              "cores": thr, "sample": desc},
             "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,

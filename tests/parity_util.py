@@ -7,7 +7,10 @@ Error measures (derived in the design notes from FP32 arithmetic):
 Storing inputs and coefficients in FP32 perturbs every output by up to
 u * sum_j |c_ij| |u_j - u_i| (u = 2^-24), which for the Laplacian reaches
 ~1e-5 of the column maximum, so the 1e-4 bar is stated normwise; the
-componentwise error (floor 1e-3 of the column maximum) is reported too.
+componentwise error (floor 1e-3 of the column maximum) is held to P99_BAR at
+its 99th percentile.  Clouds with thin 3D layers or outputs that are small
+differences of large terms are held to the plain bar with counted, bounded
+exceptions (outputs_vs_bar).
 """
 import numpy as np
 import torch
@@ -85,16 +88,16 @@ def column_error(a, b):
 
 
 def sensitivity(rp, col, coef, fields, rows=None):
-    """Per output element, sum_j |c_ij^op| |u_j - u_i| (FP64 coefficients): how
-    far a relative coefficient error of 1 can move that output.  Near-degenerate
-    rows (thin 3D layers, condition 1e3 and up) have large, cancelling
-    coefficients, so an output can be far more sensitive than its own size;
-    columns that vanish exactly (d/dz of a depth-constant field) likewise."""
+    """Per output element, sum_j |c_ij^op| |u_j - u_i| (FP64 coefficients): the
+    size of the terms an applied output is the sum of.  Near-degenerate rows
+    (thin 3D layers) and outputs that are small differences of large terms
+    (the constant Laplacian of a quadratic field) have terms far larger than
+    the output itself."""
     n = len(rp) - 1
     F = np.asarray(fields, np.float64)
     rows_of = np.repeat(np.arange(n), np.diff(rp))
     keep = np.ones(rows_of.size, bool) if rows is None else np.isin(rows_of, rows)
-    r, j, c = rows_of[keep], col[keep], np.abs(coef[keep])
+    r, j, c = rows_of[keep], col[keep], np.abs(np.asarray(coef, np.float64)[keep])
     du = np.abs(F[j] - F[r])
     b = np.zeros((n, 4, 4))
     for f in range(4):
@@ -103,17 +106,49 @@ def sensitivity(rp, col, coef, fields, rows=None):
     return b
 
 
-# Relative coefficient error each path leaves: refined FP32 stencils agree with
-# FP64 to ~1e-6 of a row's largest coefficient (about 16 unit roundoffs:
-# measured 1e-6 .. 3.5e-6 up to condition 1e5; 32 leaves 2x margin); the FP64
-# path is held to its stencil bar.
-COEF_REL = {M.F32_REFINED: 32.0 * 2.0 ** -24, M.F32_PLAIN: 2e-3, M.F64: 1e-10}
+# Outputs held to the plain normwise bar, with counted exceptions: a path that
+# evaluates the stencils from FP32 positions cannot resolve an output to better
+# than about u * (its terms' size), u = 2^-24 (the rounding of q, p(q) and w
+# alone moves the coefficients by ~1e-7 of their row), so an output whose
+# terms are 10^3 times the column's largest value can miss a 1e-4 bar.  At most
+# EXCEPTION_FRACTION of the outputs may miss it, each by no more than
+# EXCEPTION_ULPS units of roundoff of its terms.
+EXCEPTION_FRACTION = 1e-2
+EXCEPTION_ULPS = 64.0
+UNIT_ROUNDOFF = {M.F32_REFINED: 2.0 ** -24, M.F32_PLAIN: 2.0 ** -24, M.F64: 2.0 ** -53}
 
 
-def outputs_within(a, b, sens, tol, coef_rel):
-    """|a - b| <= tol * (column max of |b|) + coef_rel * sens, elementwise;
-    returns the worst ratio of the error to that allowance (<= 1 passes)."""
-    scale = np.abs(b).reshape(-1, 16).max(0)
-    allow = tol * scale + coef_rel * sens.reshape(-1, 16)
-    err = np.abs(a - b).reshape(-1, 16)
-    return float((err / np.where(allow > 0, allow, 1e-300)).max()) if err.size else 0.0
+def outputs_vs_bar(a, b, sens, dtype, zero_rel=1e-6, unit=None):
+    """The plain normwise bar TOL[dtype] per output column (field, operator),
+    with counted exceptions (see EXCEPTION_FRACTION).  A column whose FP64
+    values are all zero to rounding (largest value below zero_rel times its
+    largest term size, e.g. d/dz of a depth-constant field) has no relative
+    error; it is measured against its largest term size instead.  Returns a
+    dict; `ok` holds when the exceptions are few enough and each is bounded.
+    unit: the relative agreement of the inputs (default: the unit roundoff of
+    the path's precision)."""
+    tol = TOL[dtype]
+    a = np.asarray(a, np.float64).reshape(-1, 16)
+    b = np.asarray(b, np.float64).reshape(-1, 16)
+    sens = np.asarray(sens, np.float64).reshape(-1, 16)
+    scale = np.abs(b).max(0) if b.size else np.zeros(16)
+    term = sens.max(0) if sens.size else np.zeros(16)
+    zero = scale <= zero_rel * term
+    ref = np.where(zero, term, scale)
+    err = np.abs(a - b)
+    above = err > tol * ref
+    allow = EXCEPTION_ULPS * (UNIT_ROUNDOFF[dtype] if unit is None else unit) * sens
+    worst = float((err[above] / np.maximum(allow[above], 1e-300)).max()) if above.any() else 0.0
+    comp = err / np.maximum(np.abs(b), 1e-3 * scale)
+    p99 = np.percentile(comp[:, ~zero], 99, axis=0) if (~zero).any() and b.size else np.zeros(0)
+    n_above = int(above.sum())
+    return dict(ok=bool(n_above <= EXCEPTION_FRACTION * max(err.size, 1) and worst <= 1.0),
+                above=n_above, outputs=int(err.size), worst_exception=worst,
+                normwise=(err / np.where(ref > 0, ref, 1)).max(0) if b.size else np.zeros(16),
+                zero_columns=np.nonzero(zero)[0].tolist(), p99=p99)
+
+
+# Bar of the componentwise p99 (floor 1e-3 of the column maximum): near the
+# zero crossings of a column the componentwise error of an FP32 path is its
+# normwise error times up to 1e3, so the p99 is held to 10x the normwise bar.
+P99_BAR = {M.F32_REFINED: 1e-3, M.F32_PLAIN: 2e-2, M.F64: 1e-9}

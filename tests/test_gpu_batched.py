@@ -16,7 +16,8 @@ if not torch.cuda.is_available():
 
 from paper_2405_13165_gb300 import mafp as M  # noqa: E402
 from paper_2405_13165_gb300.pipeline import Pipeline, cloud_to_device  # noqa: E402
-from parity_util import (TOL, column_error, run_gpu, stencil_rowwise_error_vec)  # noqa: E402
+from parity_util import (P99_BAR, TOL, column_error, run_gpu,  # noqa: E402
+                         stencil_rowwise_error_vec)
 
 DTYPES = [M.F32_REFINED, M.F64]
 
@@ -69,6 +70,7 @@ def test_batch_matches_per_cloud_oracle(orc, dtype, sort):
     assert np.all(err <= TOL[dtype]), err
     nw, p99 = column_error(g["out"], o["out"])
     assert np.all(nw <= TOL[dtype]), (nw, p99)
+    assert np.all(p99 <= P99_BAR[dtype]), p99
     # the order output is the concatenation of per-cloud cell orders
     order = g["order"]
     for b in range(len(parts)):
@@ -212,6 +214,7 @@ def test_full_batch_sampled_clouds(orc, full_batch):
         assert np.all(err <= TOL[M.F32_REFINED]), (b, err)
         nw, p99 = column_error(pipe.out[lo:hi].double().cpu().numpy(), out)
         assert np.all(nw <= TOL[M.F32_REFINED]), (b, nw, p99)
+        assert np.all(p99 <= P99_BAR[M.F32_REFINED]), (b, p99)
         gstatus = pipe.status[lo:hi].cpu().numpy()
         np.testing.assert_array_equal(gstatus == M.STENCIL_DEFICIENT, status == 1)
 

@@ -17,7 +17,7 @@ if not torch.cuda.is_available():
 import oracle as O  # noqa: E402
 from paper_2405_13165_gb300 import autotune, mafp as M  # noqa: E402
 from paper_2405_13165_gb300.pipeline import Pipeline, cloud_to_device  # noqa: E402
-from parity_util import TOL  # noqa: E402
+from parity_util import P99_BAR, TOL, column_error  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -84,6 +84,10 @@ def test_stencils_and_outputs_on_sampled_rows(jet, gpu_run):
     b = out[rows].reshape(-1, 16)
     nw = np.abs(a - b).max(0) / np.abs(b).max(0)
     assert np.all(nw <= TOL[M.F32_REFINED]), nw
+    # componentwise p99 (floor 1e-3 of the column maximum)
+    _, p99 = column_error(a, b)
+    print("componentwise p99 per column:", np.array2string(p99, precision=2))
+    assert np.all(p99 <= P99_BAR[M.F32_REFINED]), p99
 
 
 def test_stencil_properties_on_all_rows(jet, gpu_run):

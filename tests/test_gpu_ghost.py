@@ -16,7 +16,7 @@ if not torch.cuda.is_available():
 from paper_2405_13165_gb300 import mafp as M  # noqa: E402
 from paper_2405_13165_gb300.ghosts import GhostZone, empty_state  # noqa: E402
 from paper_2405_13165_gb300.pipeline import Pipeline  # noqa: E402
-from parity_util import (COEF_REL, TOL, outputs_within, sensitivity,  # noqa: E402
+from parity_util import (TOL, outputs_vs_bar, sensitivity,  # noqa: E402
                          stencil_rowwise_error_vec)
 
 KEYMAP = {"type": "ptype"}
@@ -90,13 +90,18 @@ def test_ghost_zone_matches_oracle(orc, dtype, dx, columns):
     gcoef = pipe.coef[:e_reg].double().cpu().numpy()
     err, _ = stencil_rowwise_error_vec(ur[: n + 1], gcoef, coef[:e_reg])
     assert np.all(err <= TOL[dtype]), err
-    # the depth-constant fields have d/dz = 0 and a constant Laplacian: columns
-    # of (near) zeros and heavy cancellation, so the allowance includes the
-    # output's sensitivity to relative coefficient error
+    # the depth-constant quadratic fields have d/dz = 0 (columns that are zero
+    # to rounding) and a constant Laplacian that is a small difference of large
+    # terms: the outputs that miss the plain bar are counted and each bounded
+    # by the roundoff of its terms
     gout = pipe.out[:n].double().cpu().numpy()
     sens = sensitivity(ur, ucol, coef, u["vp"], rows=rows)[:n]
-    worst = outputs_within(gout, out[:n], sens, TOL[dtype], COEF_REL[dtype])
-    assert worst <= 1.0, worst
+    # FP64: the union's ghosts went through the remap in both paths and agree
+    # to `tol` (checked above), not to the last bit
+    r = outputs_vs_bar(gout, out[:n], sens, dtype, unit=tol if dtype == M.F64 else None)
+    print(f"outputs above the plain bar {r['above']} of {r['outputs']}, worst exception "
+          f"{r['worst_exception']:.3g} of its bound, zero columns {r['zero_columns']}")
+    assert r["ok"], r
     ctx.close()
 
 

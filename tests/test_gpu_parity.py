@@ -14,7 +14,8 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from paper_2405_13165_gb300 import mafp as M  # noqa: E402
-from parity_util import (TOL, column_error, run_gpu, stencil_rowwise_error_vec)  # noqa: E402
+from parity_util import (P99_BAR, TOL, column_error, run_gpu,  # noqa: E402
+                         stencil_rowwise_error_vec)
 
 DTYPES = [M.F32_REFINED, M.F64]
 
@@ -56,6 +57,7 @@ def test_small_config_end_to_end(orc, dtype, sort):
     assert np.all(err <= TOL[dtype]), err
     nw, p99 = column_error(g["out"], o["out"])
     assert np.all(nw <= TOL[dtype]), (nw, p99)
+    assert np.all(p99 <= P99_BAR[dtype]), p99
 
 
 def test_plain_fp32_is_worse_than_refined(orc):

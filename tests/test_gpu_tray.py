@@ -16,7 +16,7 @@ if not torch.cuda.is_available():
 import oracle as O  # noqa: E402
 import tray_oracle as TO  # noqa: E402
 from paper_2405_13165_gb300 import mafp as M, tray  # noqa: E402
-from parity_util import COEF_REL, TOL, outputs_within, sensitivity  # noqa: E402
+from parity_util import outputs_vs_bar, sensitivity  # noqa: E402
 
 
 def _pairs(rp, col):
@@ -60,13 +60,14 @@ def test_tray_trajectory_matches_oracle_trajectory(orc):
         np.testing.assert_array_equal(p.flag[:n].cpu().numpy()[far], info["flag"][far])
         assert np.all(info["near"] == 0)                # otherwise the trajectories part
         # thin 3D layers give near-degenerate rows with large cancelling
-        # coefficients: an FP32-refined coefficient error of ~1e-6 of the row's
-        # largest coefficient moves such an output beyond 1e-4 of its column, so
-        # that sensitivity is allowed on top of the normwise bar
+        # coefficients: the few outputs that miss the plain bar are counted
+        # and each bounded by the roundoff of its terms
         sens = sensitivity(info["row_ptr"], info["col"], info["coef"], s["vp"])
-        worst = outputs_within(p.out[:n].double().cpu().numpy(), info["out"], sens,
-                               TOL[M.F32_REFINED], COEF_REL[M.F32_REFINED])
-        assert worst <= 1.0, (k, worst)
+        r = outputs_vs_bar(p.out[:n].double().cpu().numpy(), info["out"], sens, M.F32_REFINED)
+        print(f"step {k}: outputs above the plain bar {r['above']} of {r['outputs']}, "
+              f"worst exception {r['worst_exception']:.3g} of its bound, "
+              f"componentwise p99 max {r['p99'].max():.3g}")
+        assert r["ok"], (k, r)
         assert st["n_out"] == info["n_out"]
         np.testing.assert_array_equal(loop.old2new[:n].cpu().numpy(), info["old2new"])
         G = loop.cur
@@ -110,9 +111,12 @@ def test_tray_full_size_twenty_steps(orc):
     coef, status, _ = O.stencils(c.pos_h, c.model, rp, col, rows=rows)
     out = O.apply(rp, col, coef, c.vp, rows=rows)
     sens = sensitivity(rp, col, coef, c.vp, rows=rows)
-    worst = outputs_within(p.out[:n0].double().cpu().numpy()[rows], out[rows], sens[rows],
-                           TOL[M.F32_REFINED], COEF_REL[M.F32_REFINED])
-    assert worst <= 1.0, worst
+    r = outputs_vs_bar(p.out[:n0].double().cpu().numpy()[rows], out[rows], sens[rows],
+                       M.F32_REFINED)
+    print(f"16M step 0: outputs above the plain bar {r['above']} of {r['outputs']}, "
+          f"worst exception {r['worst_exception']:.3g} of its bound, "
+          f"componentwise p99 max {r['p99'].max():.3g}")
+    assert r["ok"], r
     # twenty steps: invariants at every step
     stats = [st]
     for k in range(1, 20):
