@@ -484,7 +484,7 @@ __global__ void k_check_nnz(const long long *row_ptr, int64_t n, long long cap_n
 // (one particle) tests all candidates against itself reading them as shared
 // memory broadcasts, and writes one bit per candidate (word-major layout
 // mask[w * stride + p], coalesced across the block) plus its row length.
-// The expand kernel turns the bits back into column indices, so the distance
+// The fill kernel turns the bits back into column indices, so the distance
 // tests run once.
 constexpr int kMaskThreads = 64;
 constexpr int kMaskTile = kMaskCap + kMaskWords;   // candidates plus one pad per word
@@ -494,8 +494,8 @@ constexpr int kMaskTile = kMaskCap + kMaskWords;   // candidates plus one pad pe
 constexpr int kMaskTileSoA = kMaskCap + 2 * kMaskWords;
 constexpr int kMaskMaxP = 512;                     // particles of one cell in the mask kernel
 static_assert(kMaskCap < 65536 && kMaskMaxP % 2 == 0, "two 16-bit hit counts per word");
-constexpr int kExpThreads = 256;
-constexpr int kExpChunk = 64;             // particles of a cell expanded per round
+constexpr int kFillThreads = 256;
+constexpr int kFillChunk = 64;            // particles of a cell expanded per round
 
 // Rows of the 27-cell neighbourhood of global cell `key`: run r (dz = r/3-1,
 // dy = r%3-1) covers cells key-1..key+1 of that (y, z) row of the key's own
@@ -665,14 +665,21 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kExpThreads) k_nbr_expand(
+// Fill pass for the mask kernel's cells: one block per occupied cell, the
+// cell's particles in chunks of kFillChunk.  Staging (candidate indices, the
+// chunk's hit words and row starts) is done by the whole block with
+// independent loads, so the expansion itself reads only shared memory: one
+// warp per particle, one candidate per lane, ballot compaction into the row
+// with coalesced stores.  Rows come out ascending when the cloud is in cell
+// order (candidates are runs of consecutive sorted positions, ascending).
+__global__ void __launch_bounds__(kFillThreads) k_nbr_fill(
     CloudGrids cg, const int32_t *ucell, const int32_t *n_ucell, const int32_t *svals,
     const int32_t *cell_start, const int32_t *cell_end, const uint32_t *mask, int64_t stride,
     const long long *row_ptr, int32_t *col, long long cap_nnz, int64_t n) {
   __shared__ int r_lo[9], r_len[9], r_off[10];
-  __shared__ uint32_t mw[kMaskWords][kExpChunk];
+  __shared__ uint32_t mw[kMaskWords][kFillChunk];
   __shared__ int32_t cand_v[kMaskCap];   // original index of every candidate of the cell
+  __shared__ long long rs[kFillChunk];   // row starts of the chunk's particles
   if (!cg.all->ok) return;
   if (row_ptr[n] > cap_nnz) return;
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
@@ -683,34 +690,39 @@ __global__ void __launch_bounds__(kExpThreads) k_nbr_expand(
     const int s1 = cell_end[key];
     if (tid < 9) cell_runs(key, cg, cell_start, cell_end, tid, &r_lo[tid], &r_len[tid]);
     __syncthreads();
-    if (tid == 0) {
-      int o = 0;
-      for (int r = 0; r < 9; ++r) {
-        r_off[r] = o;
-        o += r_len[r];
+    if (tid < 32) {
+      // exclusive prefix of the 9 run lengths (lanes 0..8), shuffles only
+      const int v = tid < 9 ? r_len[tid] : 0;
+      int inc = v;
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (tid >= o) inc += u;
       }
-      r_off[9] = o;
+      if (tid < 9) r_off[tid] = inc - v;
+      if (tid == 8) r_off[9] = inc;
     }
     __syncthreads();
     const int total = r_off[9];
-    if (total <= kMaskCap && s1 - s0 <= kMaskMaxP) {   // the mask kernel's cells
+    const int P = s1 - s0;
+    if (total <= kMaskCap && P <= kMaskMaxP) {   // the mask kernel's cells
       for (int r = 0; r < 9; ++r)
-        for (int t = tid; t < r_len[r]; t += kExpThreads) cand_v[r_off[r] + t] = svals[r_lo[r] + t];
+        for (int t = tid; t < r_len[r]; t += kFillThreads) cand_v[r_off[r] + t] = svals[r_lo[r] + t];
       const int nwords = (total + 31) >> 5;
-      for (int p0 = s0; p0 < s1; p0 += kExpChunk) {
-        const int np = min(kExpChunk, s1 - p0);
-        for (int k = tid; k < nwords * kExpChunk; k += kExpThreads) {
-          const int w = k / kExpChunk, q = k % kExpChunk;
-          mw[w][q] = q < np ? mask[(int64_t)w * stride + p0 + q] : 0u;
+      for (int p0 = 0; p0 < P; p0 += kFillChunk) {
+        const int np = min(kFillChunk, P - p0);
+        for (int k = tid; k < nwords * kFillChunk; k += kFillThreads) {
+          const int w = k / kFillChunk, q = k % kFillChunk;
+          mw[w][q] = q < np ? mask[(int64_t)w * stride + s0 + p0 + q] : 0u;
         }
+        for (int q = tid; q < np; q += kFillThreads) rs[q] = row_ptr[svals[s0 + p0 + q]];
         __syncthreads();
-        // one warp per particle, one candidate per lane: ballot compaction
-        for (int q = wp; q < np; q += kExpThreads / 32) {
-          long long at = row_ptr[svals[p0 + q]];
+        for (int q = wp; q < np; q += kFillThreads / 32) {
+          int32_t *crow = col + rs[q];
+          int at = 0;
           for (int w = 0; w < nwords; ++w) {
             const uint32_t word = mw[w][q];
-            const bool hit = (word >> lane) & 1u;
-            if (hit) col[at + __popc(word & lt)] = cand_v[(w << 5) + lane];
+            if ((word >> lane) & 1u) crow[at + __popc(word & lt)] = cand_v[(w << 5) + lane];
             at += __popc(word);
           }
         }
@@ -884,8 +896,8 @@ static int build_neighbours_t(mafp_ctx *ctx, int64_t n, int nb, const long long 
   MAFP_TIMED(ctx, s, "k_check_nnz",
              k_check_nnz<<<1, 1, 0, s>>>(reinterpret_cast<const long long *>(row_ptr), n, cap_nnz, nnz_dev,
                               ctx->d_status, ctx->d_grid));
-  MAFP_TIMED(ctx, s, "k_nbr_expand",
-             k_nbr_expand<T><<<sms * 16, kExpThreads, 0, s>>>(
+  MAFP_TIMED(ctx, s, "k_nbr_fill",
+             k_nbr_fill<<<sms * 8, kFillThreads, 0, s>>>(
                  cg, ctx->ucell, ctx->n_ucell, vin, ctx->cell_start, ctx->cell_end,
                  ctx->nbr_mask, stride, reinterpret_cast<const long long *>(row_ptr), col,
                  cap_nnz, n));

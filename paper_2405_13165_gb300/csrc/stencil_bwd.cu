@@ -21,8 +21,8 @@
 // Ps = sum_j z_j z_j^T (z_j = y_j - y_c, y_j = (x_j - x_i)/h) give
 //   dL/dy_j = sum_k beta_k (t_k (n.z_j) + n (t_k.z_j)),  beta_k = (tbar_k.n)/(l_k - l3),
 // with l_k = t_k^T Ps t_k (Rayleigh quotients in the given frame).  The gradient
-// pass sums n.tbar_k; a third pass over the row sums y_j and y_j y_j^T and a
-// fourth scatters the term.
+// pass also sums n.tbar_k and the neighbours' frame coordinates and their
+// squares; a third pass over the row scatters the term.
 #include "internal.cuh"
 #include "stencil_common.cuh"
 
@@ -202,6 +202,9 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
   const C a2 = C(-2) * sp.alpha * sp.inv_den;  // W'(s)/s = a2 exp(-alpha s^2)
   C acc_i[3] = {0, 0, 0};
   C tn1 = 0, tn2 = 0;   // film rows: n . dL/dt1 and n . dL/dt2 at fixed n
+  // film rows: sums of the frame coordinates (xi, eta, zeta) = y.(t1, t2, n) of
+  // the neighbours and of their squares (the PCA's Rayleigh quotients)
+  C sc[3] = {0, 0, 0}, sq[3] = {0, 0, 0};
   for (long long e0 = b + lane; e0 < e1; e0 += kGradGatherC * G) {
     V xs[kGradGatherC], fs[kGradGatherC];
     int js[kGradGatherC];
@@ -260,6 +263,9 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
       const C gn = g4[0] * nv[0] + g4[1] * nv[1] + g4[2] * nv[2];
       tn1 += (xb * dn + w * s01[0] * gn) * hinv;
       tn2 += (eb * dn + w * s01[1] * gn) * hinv;
+      const C ze = dn * hinv;
+      sc[0] += xi_; sc[1] += et_; sc[2] += ze;
+      sq[0] += xi_ * xi_; sq[1] += et_ * et_; sq[2] += ze * ze;
     }
     add_xyz<TS>(gpos + 4 * (int64_t)j, TS(d[0]), TS(d[1]), TS(d[2]));
 #pragma unroll
@@ -268,53 +274,50 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
   }
   if constexpr (M == 6) {
     // ---- pass 3 (film rows): the PCA frame's dependence on the positions.
-    // First sum_j y_j and sum_j y_j y_j^T (xx, yy, zz, xy, xz, yz) over the
-    // same-model part of the row (a separate pass keeps these sums out of the
-    // registers of the two heavy passes), then scatter the frame term.
+    // With the frame coordinates' sums from pass 2, the centroid is
+    // y_c = xc t1 + ec t2 + zc n and l_k - l3 follow from the Rayleigh
+    // quotients; one more pass over the row scatters the term.
     tn1 = group_sum<G>(tn1);
     tn2 = group_sum<G>(tn2);
-    C sy[3] = {0, 0, 0}, syy[6] = {0, 0, 0, 0, 0, 0};
-    for (long long e = b + lane; e < e1; e += G) {
-      const int j = col[e];
-      if (j == i || model[j] != mi) continue;
-      const V xj = ld4(pos + j);
-      const C y0 = (C(xj.x) - C(xi.x)) * hinv, y1 = (C(xj.y) - C(xi.y)) * hinv,
-              y2 = (C(xj.z) - C(xi.z)) * hinv;
-      sy[0] += y0; sy[1] += y1; sy[2] += y2;
-      syy[0] += y0 * y0; syy[1] += y1 * y1; syy[2] += y2 * y2;
-      syy[3] += y0 * y1; syy[4] += y0 * y2; syy[5] += y1 * y2;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      sc[a] = group_sum<G>(sc[a]);
+      sq[a] = group_sum<G>(sq[a]);
     }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) sy[a] = group_sum<G>(sy[a]);
-#pragma unroll
-    for (int a = 0; a < 6; ++a) syy[a] = group_sum<G>(syy[a]);
     const C inv_m = C(1) / C(cnt);
-    const C yc[3] = {sy[0] * inv_m, sy[1] * inv_m, sy[2] * inv_m};
-    // Ps = sum_j y_j y_j^T - m y_c y_c^T, quadratic form v^T Ps v
-    auto quad = [&](const C (&v)[3]) {
-      const C vy = v[0] * sy[0] + v[1] * sy[1] + v[2] * sy[2];
-      const C q = v[0] * v[0] * syy[0] + v[1] * v[1] * syy[1] + v[2] * v[2] * syy[2] +
-                  C(2) * (v[0] * v[1] * syy[3] + v[0] * v[2] * syy[4] + v[1] * v[2] * syy[5]);
-      return q - vy * vy * inv_m;
-    };
-    const C l3 = quad(nv), g1 = quad(t1) - l3, g2 = quad(t2) - l3;
+    const C xc = sc[0] * inv_m, ec = sc[1] * inv_m, zc = sc[2] * inv_m;
+    const C l3 = sq[2] - sc[2] * zc;
+    const C g1 = (sq[0] - sc[0] * xc) - l3, g2 = (sq[1] - sc[1] * ec) - l3;
     const C be1 = g1 > C(0) ? tn1 / g1 : C(0);
     const C be2 = g2 > C(0) ? tn2 / g2 : C(0);
-    for (long long e = b + lane; e < e1; e += G) {
-      const int j = col[e];
-      if (j == i || model[j] != mi) continue;
-      const V xj = ld4(pos + j);
-      const C z0 = (C(xj.x) - C(xi.x)) * hinv - yc[0], z1 = (C(xj.y) - C(xi.y)) * hinv - yc[1],
-              z2 = (C(xj.z) - C(xi.z)) * hinv - yc[2];
-      const C nz = nv[0] * z0 + nv[1] * z1 + nv[2] * z2;
-      const C u1 = be1 * (t1[0] * z0 + t1[1] * z1 + t1[2] * z2);
-      const C u2 = be2 * (t2[0] * z0 + t2[1] * z1 + t2[2] * z2);
-      C d[3];
+    // dL/dx_j = ((be1 t1 + be2 t2) (n.z_j) + n (be1 t1.z_j + be2 t2.z_j)) / h
+    C av[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) d[a] = ((be1 * t1[a] + be2 * t2[a]) * nz + nv[a] * (u1 + u2)) * hinv;
-      add_xyz<TS>(gpos + 4 * (int64_t)j, TS(d[0]), TS(d[1]), TS(d[2]));
+    for (int a = 0; a < 3; ++a) av[a] = (be1 * t1[a] + be2 * t2[a]) * hinv;
+    const C bn1 = be1 * hinv, bn2 = be2 * hinv;
+    constexpr int U = 4;
+    for (long long e0 = b + lane; e0 < e1; e0 += U * G) {
+      V xs[U];
+      bool oks[U];
+      gather_row<U, G>(e0, e1, i, mi, col, pos, model, xs, oks);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) acc_i[a] -= d[a];
+      for (int u = 0; u < U; ++u) {
+        const long long e = e0 + (long long)u * G;
+        if (!oks[u]) continue;
+        const int j = col[e];
+        if (j == i) continue;
+        const C dx = C(xs[u].x) - C(xi.x), dy = C(xs[u].y) - C(xi.y), dz = C(xs[u].z) - C(xi.z);
+        const C zn = (dx * nv[0] + dy * nv[1] + dz * nv[2]) * hinv - zc;
+        const C z1 = (dx * t1[0] + dy * t1[1] + dz * t1[2]) * hinv - xc;
+        const C z2 = (dx * t2[0] + dy * t2[1] + dz * t2[2]) * hinv - ec;
+        const C tz = bn1 * z1 + bn2 * z2;
+        C d[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) d[a] = av[a] * zn + nv[a] * tz;
+        add_xyz<TS>(gpos + 4 * (int64_t)j, TS(d[0]), TS(d[1]), TS(d[2]));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc_i[a] -= d[a];
+      }
     }
   }
 #pragma unroll
