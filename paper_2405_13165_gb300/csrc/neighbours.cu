@@ -897,7 +897,7 @@ static int build_neighbours_t(mafp_ctx *ctx, int64_t n, int nb, const long long 
              k_check_nnz<<<1, 1, 0, s>>>(reinterpret_cast<const long long *>(row_ptr), n, cap_nnz, nnz_dev,
                               ctx->d_status, ctx->d_grid));
   MAFP_TIMED(ctx, s, "k_nbr_fill",
-             k_nbr_fill<<<sms * 8, kFillThreads, 0, s>>>(
+             k_nbr_fill<<<sms * (2048 / kFillThreads), kFillThreads, 0, s>>>(
                  cg, ctx->ucell, ctx->n_ucell, vin, ctx->cell_start, ctx->cell_end,
                  ctx->nbr_mask, stride, reinterpret_cast<const long long *>(row_ptr), col,
                  cap_nnz, n));
