@@ -486,7 +486,7 @@ __global__ void k_check_nnz(const long long *row_ptr, int64_t n, long long cap_n
 // mask[w * stride + p], coalesced across the block) plus its row length.
 // The fill kernel turns the bits back into column indices, so the distance
 // tests run once.
-constexpr int kMaskThreads = 64;
+constexpr int kMaskThreads = 128;
 constexpr int kMaskTile = kMaskCap + kMaskWords;   // candidates plus one pad per word
 // FP32 tile as four arrays (x, y, z, h/2), two pad floats per word of 32
 // candidates: a float2 read gives two consecutive candidates, and the words
