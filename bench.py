@@ -72,8 +72,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mafp", choices=["mafp", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000, help="particle count of the jet cloud")
-    ap.add_argument("--cpu-sample", type=int, default=1_000_000,
-                    help="particles of the CPU-oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="particles of the CPU-oracle sample (0: the whole cloud)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -148,7 +148,7 @@ def cpu_oracle_sample(cloud, m: int):
     OpenMP over particles on every host core.  Returns (seconds, threads,
     description, particles, the oracle's applied outputs)."""
     import oracle
-    sub = cloud.take(np.arange(min(m, cloud.n)))
+    sub = cloud.take(np.arange(min(m, cloud.n) if m > 0 else cloud.n))
     t0 = time.perf_counter()
     rp, col = oracle.neighbours(sub.pos_h)
     cl = oracle.classify(sub.pos_h, sub.model, sub.ptype, sub.normal, sub.vol, sub.h3d,

@@ -81,6 +81,10 @@ typedef struct {
                               16 or 32 (the FP64 adjoint takes at least 8) */
   int32_t grad2d_group;    /* lanes per 2D particle in mafp_build_stencils_backward: 2, 4,
                               8 or 16 */
+  int32_t cell_edge_pct;   /* cell tile of the neighbour search: the grid's cell edge in
+                              percent of the cloud's largest h, 100..200 (larger cells:
+                              more candidates per particle, fewer cells to stage); the
+                              neighbour sets are the same for every value */
 } mafp_tuning;
 
 /* Device-side status block, copied out by mafp_get_status. */

@@ -1,5 +1,6 @@
-"""Autotuner of the launch shapes (lanes per particle / per row) of
-build_stencils and apply_ops.
+"""Autotuner of the launch shapes: the neighbour search's cell tile (cell edge
+in percent of max h) and the lanes per particle / per row of build_stencils,
+apply_ops and the stencil adjoint.
 
 For a cloud already on the device it times every supported group size of a
 stage with CUDA events (a few repetitions, best taken), keeps the fastest,
@@ -19,7 +20,7 @@ from . import mafp as M
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
 CHOICES = {"stencil3d_group": (8, 16, 32), "stencil2d_group": (4, 8, 16),
            "apply_group": (4, 8, 16), "grad3d_group": (4, 8, 16, 32),
-           "grad2d_group": (2, 4, 8, 16)}
+           "grad2d_group": (2, 4, 8, 16), "cell_edge_pct": (100, 115, 130)}
 
 
 def mix_key(d, pipe, n: int) -> str:
@@ -58,6 +59,15 @@ def tune(ctx: M.Context, pipe, d, use_cache: bool = True, verbose: bool = False)
         return cache[key]
     timings = {}
     best = dict(ctx.tuning())
+    # cell tile of the neighbour search (the lists are the same for every edge)
+    res = {}
+    for pct in CHOICES["cell_edge_pct"]:
+        ctx.set_tuning(**{**best, "cell_edge_pct": pct})
+        res[pct] = _time(lambda: pipe.neighbours(d))
+    best["cell_edge_pct"] = min(res, key=res.get)
+    timings["cell_edge_pct"] = res
+    ctx.set_tuning(**best)
+    pipe.neighbours(d)
     for knob in ("stencil3d_group", "stencil2d_group"):
         res = {}
         for g in CHOICES[knob]:

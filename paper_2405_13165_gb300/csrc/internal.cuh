@@ -207,6 +207,7 @@ inline void default_tuning(mafp_tuning *t) {
   t->apply_group = 8;
   t->grad3d_group = 4;
   t->grad2d_group = 2;
+  t->cell_edge_pct = 100;
 }
 
 // Name of a kernel instance for the timing record: built once (function-local

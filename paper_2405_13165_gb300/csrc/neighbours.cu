@@ -140,13 +140,15 @@ __device__ double cloud_cells(const double v[8], double c, int dim[3]) {
 
 // One block: per-cloud grids from the folded boxes, the global cell numbering
 // (exclusive scan of the clouds' cell counts) and the all-clouds flag.  The cell
-// edge of every cloud starts strictly above its max h (so S_i lies in the 27
-// cells around i's cell) and grows uniformly when the total exceeds cap_cells.
+// edge of every cloud starts strictly above its max h times edge_factor >= 1
+// (so S_i lies in the 27 cells around i's cell) and grows uniformly when the
+// total exceeds cap_cells.
 __global__ void __launch_bounds__(kBoxThreads) k_cloud_grid(double *partial,
                                                             const long long *off, int64_t n,
                                                             int nb, int parts, GridDev *grids,
                                                             long long *cell_base, GridDev *all,
-                                                            DevStatus *st, long long cap_cells) {
+                                                            DevStatus *st, long long cap_cells,
+                                                            double edge_factor) {
   __shared__ double s_nonfinite, s_cells;
   __shared__ double s_scale;
   __shared__ int s_bad;
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_cloud_grid(double *partial,
       double v[8];
       for (int k = 0; k < 8; ++k) v[k] = partial[(long long)b * parts * 8 + k];
       int dim[3];
-      const double c = v[6] * (1.0 + 1e-6) * s_scale;
+      const double c = v[6] * (1.0 + 1e-6) * edge_factor * s_scale;
       const double cells = cloud_cells(v, c, dim);
       GridDev &g = grids[b];
       for (int a = 0; a < 3; ++a) g.lo[a] = v[a] < INFINITY ? v[a] : 0.0;
@@ -826,7 +828,8 @@ static int sort_into_cells_t(mafp_ctx *ctx, int64_t n, int nb, const long long *
              k_cloud_grid<<<1, kBoxThreads, 0, s>>>(ctx->cloud_partial, cloud_off, n, nb, parts,
                                                     ctx->d_grids,
                                                     ctx->cell_base, ctx->d_grid, ctx->d_status,
-                                                    ctx->cap_cells));
+                                                    ctx->cap_cells,
+                                                    0.01 * (double)ctx->tune.cell_edge_pct));
   CloudGrids cg{ctx->d_grids, ctx->cell_base, nb, ctx->d_grid};
   MAFP_TIMED(ctx, s, "k_hash",
              k_hash<T><<<grid_for(n, 256, sms * 16), 256, 0, s>>>(pos, n, ctx->cloud_id, cg,

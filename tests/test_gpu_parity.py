@@ -238,3 +238,27 @@ def test_launch_shapes_agree_with_oracle(orc, g3, g2, ga):
     assert np.all(err <= TOL[M.F32_REFINED]), err
     nw, p99 = column_error(g["out"], o["out"])
     assert np.all(nw <= TOL[M.F32_REFINED]), (nw, p99)
+
+
+@pytest.mark.parametrize("pct", [100, 115, 130, 200])
+def test_cell_tile_shapes_give_the_oracle_lists(orc, pct):
+    """Every cell edge of the neighbour grid (cell_edge_pct, the autotuner's cell
+    tile) gives the oracle's neighbour lists bit for bit, in cell order and
+    unsorted (cells whose candidate union overflows the mask tile take the
+    warp-per-particle path)."""
+    for c in (C.cell_sorted(C.config_small()), C.random_cloud(3000, 11)):
+        rp, col = orc.neighbours(c.pos_h)
+        ctx = M.Context(c.n)
+        ctx.set_tuning(cell_edge_pct=pct)
+        g, *_ = run_gpu(c, M.F32_REFINED, ctx=ctx, stages=("nbr",))
+        assert g["status_block"]["code"] == 0
+        np.testing.assert_array_equal(g["row_ptr"], rp)
+        np.testing.assert_array_equal(g["col"], col)
+        h = float(c.pos_h[:, 3].max())
+        assert g["status_block"]["cell_size"] >= pct / 100.0 * h
+        ctx.close()
+    ctx = M.Context(16)
+    for bad in (99, 201):
+        with pytest.raises(M.MafpError):
+            ctx.set_tuning(cell_edge_pct=bad)
+    ctx.close()
