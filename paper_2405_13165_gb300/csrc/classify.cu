@@ -90,6 +90,82 @@ __device__ void row_scatter(int64_t i, const V *pos, const uint8_t *model,
   for (int k = 0; k < 6; ++k) cov[k] = group_sum<G>(a[k]);
 }
 
+// FP32 path: the same row in one pass -- the counts, neighbour flags and
+// Eq. Height of row_pass1 together with the raw second moments sum_j q_j q_j^T,
+// two neighbours gathered ahead per lane; the scatter matrix is formed from
+// the moments as sum_j q_j q_j^T - m q_c q_c^T.  (Coordinates are O(1) after
+// the scaling by h and the particle sits inside its neighbourhood, so the
+// difference loses little; decisions near a threshold are retaken in FP64
+// with the two-pass form.)
+template <int G, typename V, typename TV>
+__device__ void row_one_pass(int64_t i, const V *pos, const uint8_t *model, const uint8_t *type,
+                             const TV *vol, const long long *row_ptr, const int32_t *col,
+                             float alpha, int *m_out, float cov[6], float qc[3], float *H_out,
+                             int *fs_out, int *in_out) {
+  constexpr int U = 2;
+  const int lane = threadIdx.x & (G - 1);
+  const V xi = ld4(pos + i);
+  const uint8_t mi = model[i];
+  const float hinv = 1.0f / xi.w;
+  const float api = alpha / 3.141592653589793f;
+  float s[3] = {0, 0, 0}, a[6] = {0, 0, 0, 0, 0, 0}, H = 0;
+  int m = 0, fs = 0, in = 0;
+  const long long e1 = row_ptr[i + 1];
+  for (long long e0 = row_ptr[i] + lane; e0 < e1; e0 += U * G) {
+    int js[U];
+    V xs[U];
+    uint8_t ms[U], ts[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) js[u] = e0 + u * G < e1 ? col[e0 + u * G] : -1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = js[u] >= 0 ? js[u] : (int)i;
+      xs[u] = ld4(pos + j);
+      ms[u] = model[j];
+      ts[u] = type[j];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = js[u];
+      if (j < 0 || ms[u] != mi) continue;
+      const float dx = xs[u].x - xi.x, dy = xs[u].y - xi.y, dz = xs[u].z - xi.z;
+      const float qx = dx * hinv, qy = dy * hinv, qz = dz * hinv;
+      s[0] += qx; s[1] += qy; s[2] += qz;
+      a[0] += qx * qx; a[1] += qy * qy; a[2] += qz * qz;
+      a[3] += qx * qy; a[4] += qx * qz; a[5] += qy * qz;
+      ++m;
+      if (mi == MAFP_MODEL_2D) {
+        if (vol) {
+          const float d2 = (dx * dx + dy * dy) + dz * dz;
+          const float hj = xs[u].w;
+          const float ih2 = 1.0f / (hj * hj);
+          H += api * ih2 * expf(-alpha * d2 * ih2) * float(vol[j]);
+        }
+      } else if (j != i) {
+        fs |= ts[u] == MAFP_TYPE_FREE_SURFACE;
+        in |= ts[u] == MAFP_TYPE_INTERIOR;
+      }
+    }
+  }
+  m = group_sum<G>(m);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s[k] = group_sum<G>(s[k]);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) a[k] = group_sum<G>(a[k]);
+  *H_out = group_sum<G>(H);
+  *fs_out = group_any<G>(fs);
+  *in_out = group_any<G>(in);
+  *m_out = m;
+  const float im = m > 0 ? 1.0f / (float)m : 0.0f;
+  qc[0] = s[0] * im; qc[1] = s[1] * im; qc[2] = s[2] * im;
+  cov[0] = a[0] - s[0] * qc[0];
+  cov[1] = a[1] - s[1] * qc[1];
+  cov[2] = a[2] - s[2] * qc[2];
+  cov[3] = a[3] - s[0] * qc[1];
+  cov[4] = a[4] - s[0] * qc[2];
+  cov[5] = a[5] - s[1] * qc[2];
+}
+
 // FP64 PCA of particle i (the retake path): centroid, scatter, Jacobi.
 template <int G, typename V>
 __device__ void pca64(int64_t i, const V *pos, const uint8_t *model, const uint8_t *type,
@@ -136,13 +212,19 @@ __global__ void __launch_bounds__(kClsThreads, sizeof(T) == 4 ? 8 : 1) k_classif
     if (mi == MAFP_MODEL_2D || ti == MAFP_TYPE_WALL) {
       did_pca = true;
       int m, fs, in;
-      T qs[3];
-      row_pass1<G, T>(i, pos, model, type, vol, row_ptr, col, (T)prm.alpha_film, &m, qs, &H, &fs,
-                      &in);
-      const T im = m > 0 ? T(1) / T(m) : T(0);
-      const T qc[3] = {qs[0] * im, qs[1] * im, qs[2] * im};
       T cov[6];
-      row_scatter<G, T>(i, pos, model, row_ptr, col, qc, cov);
+      if constexpr (sizeof(T) == 4) {
+        float qc[3];
+        row_one_pass<G>(i, pos, model, type, vol, row_ptr, col, (float)prm.alpha_film, &m, cov,
+                        qc, &H, &fs, &in);
+      } else {
+        T qs[3];
+        row_pass1<G, T>(i, pos, model, type, vol, row_ptr, col, (T)prm.alpha_film, &m, qs, &H,
+                        &fs, &in);
+        const T im = m > 0 ? T(1) / T(m) : T(0);
+        const T qc[3] = {qs[0] * im, qs[1] * im, qs[2] * im};
+        row_scatter<G, T>(i, pos, model, row_ptr, col, qc, cov);
+      }
       T gap = 0;
       if constexpr (sizeof(T) == 4) {
         eig3_closed(cov, lam, W, &gap);
