@@ -77,8 +77,8 @@ typedef struct {
   int32_t stencil3d_group; /* lanes per 3D particle in mafp_build_stencils: 8, 16 or 32 */
   int32_t stencil2d_group; /* lanes per 2D particle in mafp_build_stencils: 4, 8 or 16 */
   int32_t apply_group;     /* lanes per row in mafp_apply_ops / _backward: 4, 8 or 16 */
-  int32_t grad3d_group;    /* lanes per 3D particle in mafp_build_stencils_backward: 4, 8,
-                              16 or 32 (the FP64 adjoint takes at least 8) */
+  int32_t grad3d_group;    /* lanes per 3D particle in mafp_build_stencils_backward: 2, 4,
+                              8, 16 or 32 (the FP64 adjoint takes at least 8) */
   int32_t grad2d_group;    /* lanes per 2D particle in mafp_build_stencils_backward: 2, 4,
                               8 or 16 */
   int32_t cell_edge_pct;   /* cell tile of the neighbour search: the grid's cell edge in

@@ -19,7 +19,7 @@ from . import mafp as M
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
 CHOICES = {"stencil3d_group": (8, 16, 32), "stencil2d_group": (4, 8, 16),
-           "apply_group": (4, 8, 16), "grad3d_group": (4, 8, 16, 32),
+           "apply_group": (4, 8, 16), "grad3d_group": (2, 4, 8, 16, 32),
            "grad2d_group": (2, 4, 8, 16), "cell_edge_pct": (100, 115, 130)}
 
 

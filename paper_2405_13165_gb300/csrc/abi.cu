@@ -211,7 +211,8 @@ int mafp_set_tuning(mafp_ctx *ctx, const mafp_tuning *t) {
   if (!(g3 == 8 || g3 == 16 || g3 == 32)) return fail(ctx, MAFP_EINVAL, "stencil3d_group");
   if (!(g2 == 4 || g2 == 8 || g2 == 16)) return fail(ctx, MAFP_EINVAL, "stencil2d_group");
   if (!(ga == 4 || ga == 8 || ga == 16)) return fail(ctx, MAFP_EINVAL, "apply_group");
-  if (!(gb == 4 || gb == 8 || gb == 16 || gb == 32)) return fail(ctx, MAFP_EINVAL, "grad3d_group");
+  if (!(gb == 2 || gb == 4 || gb == 8 || gb == 16 || gb == 32))
+    return fail(ctx, MAFP_EINVAL, "grad3d_group");
   if (!(gf == 2 || gf == 4 || gf == 8 || gf == 16)) return fail(ctx, MAFP_EINVAL, "grad2d_group");
   if (t->cell_edge_pct < 100 || t->cell_edge_pct > 200) return fail(ctx, MAFP_EINVAL, "cell_edge_pct");
   ctx->tune = *t;

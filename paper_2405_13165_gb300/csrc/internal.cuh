@@ -205,7 +205,7 @@ inline void default_tuning(mafp_tuning *t) {
   t->stencil3d_group = 32;
   t->stencil2d_group = 8;
   t->apply_group = 8;
-  t->grad3d_group = 4;
+  t->grad3d_group = 2;
   t->grad2d_group = 2;
   t->cell_edge_pct = 100;
 }

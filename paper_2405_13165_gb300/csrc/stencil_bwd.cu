@@ -385,13 +385,19 @@ static void launch_grad_g(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void *
 }
 
 // Group sizes: grad3d_group for 3D particles (at least 8 in FP64, where the
-// 4-lane instance would spill its registers), grad2d_group for 2D ones.
+// 2- and 4-lane instances would spill their registers), grad2d_group for 2D ones.
 template <typename TS, typename C, bool QUEUE>
 static void launch_grad(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void *pos_h,
                         const uint8_t *model, const void *frame, const long long *rp,
                         const int32_t *col, const void *fields, const void *gout, void *gpos,
                         const StParams<C> &sp) {
   switch (ctx->tune.grad3d_group) {
+    case 2:
+      if constexpr (sizeof(TS) == 4) {
+        launch_grad_g<TS, C, 10, 2, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp);
+        break;
+      }
+      [[fallthrough]];
     case 4:
       if constexpr (sizeof(TS) == 4) {
         launch_grad_g<TS, C, 10, 4, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp);

@@ -160,8 +160,8 @@ def test_fp64_film_gradient_matches_central_differences(shape_name):
 @pytest.mark.parametrize("dtype", [M.F32_REFINED, M.F64])
 def test_adjoint_launch_shapes_agree_with_oracle(dtype):
     """Every grad3d_group / grad2d_group (lanes per 3D / film particle of the
-    position adjoint) gives the oracle's gradient; in FP64 the 4-lane 3D choice
-    runs the 8-lane kernel."""
+    position adjoint) gives the oracle's gradient; in FP64 the 2- and 4-lane 3D
+    choices run the 8-lane kernel."""
     c = C.cube_on_sheet(0.04, cube=0.32, sheet=1.0)
     ctx, d, rp, col, frame = _setup(c, dtype)
     rng = np.random.default_rng(11)
@@ -173,7 +173,7 @@ def test_adjoint_launch_shapes_agree_with_oracle(dtype):
     tol = 2e-3 if dtype != M.F64 else 1e-8
     gout = torch.tensor(Gr, dtype=d["pos_h"].dtype, device="cuda").contiguous()
     gpos = torch.empty_like(d["pos_h"])
-    for gb, gf in ((4, 2), (8, 4), (16, 8), (32, 16)):
+    for gb, gf in ((2, 2), (4, 2), (8, 4), (16, 8), (32, 16)):
         ctx.set_tuning(grad3d_group=gb, grad2d_group=gf)
         assert ctx.tuning()["grad3d_group"] == gb and ctx.tuning()["grad2d_group"] == gf
         gpos.fill_(float("nan"))
@@ -184,7 +184,7 @@ def test_adjoint_launch_shapes_agree_with_oracle(dtype):
         assert np.all(err <= tol * scale), (gb, err / scale)
         assert np.all(got[:, 3] == 0)
     with pytest.raises(M.MafpError):
-        ctx.set_tuning(grad3d_group=2)
+        ctx.set_tuning(grad3d_group=1)
     with pytest.raises(M.MafpError):
         ctx.set_tuning(grad2d_group=32)
     ctx.close()
