@@ -270,7 +270,8 @@ __global__ void k_clear_cells(const GridDev *g, int32_t *cell_start, int32_t *ce
                               int32_t *n_ucell) {
   if (!g->ok) return;
   const long long nc = g->ncells;
-  if (blockIdx.x == 0 && threadIdx.x == 0) n_ucell[0] = n_ucell[1] = 0;
+  // occupied cells, overflow cells, and the work tickets of the mask and fill kernels
+  if (blockIdx.x == 0 && threadIdx.x == 0) n_ucell[0] = n_ucell[1] = n_ucell[2] = n_ucell[3] = 0;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nc;
        k += (long long)gridDim.x * blockDim.x) {
     cell_start[k] = INT_MAX;
@@ -545,7 +546,7 @@ __device__ __forceinline__ bool support_test(const double4_16a &a, const double4
 
 template <typename T>
 __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
-    CloudGrids cg, const int32_t *ucell, const int32_t *n_ucell, const vec4_t<T> *spos,
+    CloudGrids cg, const int32_t *ucell, int32_t *n_ucell, const vec4_t<T> *spos,
     const int32_t *svals, const int32_t *cell_start, const int32_t *cell_end, int32_t *counts,
     uint32_t *mask, int64_t stride, int32_t *overflow, int32_t *n_overflow) {
   using V = vec4_t<T>;
@@ -557,11 +558,17 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
   // per-particle hit counts, two 16-bit counts per word (a row has at most
   // kMaskCap < 65536 candidates), so the FP32 tile and these fit 8 blocks per SM
   __shared__ unsigned cnt_s[kMaskMaxP / 2];
-  __shared__ int s_ovf;
+  __shared__ int s_ovf, s_cb;
   if (!cg.all->ok) return;
   const int tid = threadIdx.x;
-  const int nu = *n_ucell;
-  for (int cb = blockIdx.x; cb < nu; cb += gridDim.x) {
+  const int nu = n_ucell[0];
+  for (;;) {
+    // cells are handed out one at a time (work ticket n_ucell[2]): a block that
+    // finishes a light film cell takes the next cell at once
+    if (tid == 0) s_cb = atomicAdd(n_ucell + 2, 1);
+    __syncthreads();
+    const int cb = s_cb;
+    if (cb >= nu) break;
     const int key = ucell[2 * cb], s0 = ucell[2 * cb + 1];
     const int s1 = cell_end[key];
     if (tid < 9) cell_runs(key, cg, cell_start, cell_end, tid, &r_lo[tid], &r_len[tid]);
@@ -675,19 +682,24 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
 // with coalesced stores.  Rows come out ascending when the cloud is in cell
 // order (candidates are runs of consecutive sorted positions, ascending).
 __global__ void __launch_bounds__(kFillThreads) k_nbr_fill(
-    CloudGrids cg, const int32_t *ucell, const int32_t *n_ucell, const int32_t *svals,
+    CloudGrids cg, const int32_t *ucell, int32_t *n_ucell, const int32_t *svals,
     const int32_t *cell_start, const int32_t *cell_end, const uint32_t *mask, int64_t stride,
     const long long *row_ptr, int32_t *col, long long cap_nnz, int64_t n) {
   __shared__ int r_lo[9], r_len[9], r_off[10];
   __shared__ uint32_t mw[kMaskWords][kFillChunk];
   __shared__ int32_t cand_v[kMaskCap];   // original index of every candidate of the cell
   __shared__ long long rs[kFillChunk];   // row starts of the chunk's particles
+  __shared__ int s_cb;
   if (!cg.all->ok) return;
   if (row_ptr[n] > cap_nnz) return;
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  const int nu = *n_ucell;
-  for (int cb = blockIdx.x; cb < nu; cb += gridDim.x) {
+  const int nu = n_ucell[0];
+  for (;;) {
+    if (tid == 0) s_cb = atomicAdd(n_ucell + 3, 1);   // work ticket, as in the mask kernel
+    __syncthreads();
+    const int cb = s_cb;
+    if (cb >= nu) break;
     const int key = ucell[2 * cb], s0 = ucell[2 * cb + 1];
     const int s1 = cell_end[key];
     if (tid < 9) cell_runs(key, cg, cell_start, cell_end, tid, &r_lo[tid], &r_len[tid]);
