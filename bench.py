@@ -246,6 +246,7 @@ def bench_gpu(args):
         # output (the flags), e.g. the download of the previous step's results
         nonlocal have_bwd
         d = dsrc if src is None else src
+        stream = torch.cuda.current_stream()   # the capturing stream inside a graph capture
         side = stream if serial else side_stream
         sin = state_in if src is None else {**{k: src[k] for k in state_in if k != "type"},
                                             "type": src["ptype"]}
@@ -305,6 +306,17 @@ def bench_gpu(args):
     if st["code"] != 0:
         raise RuntimeError(f"device status after warm-up: {st}")
 
+    # the whole step (both streams) captured once in a CUDA graph and replayed
+    gstream = torch.cuda.Stream(dev)
+    gstream.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gstream):
+        step()
+    stream.wait_stream(gstream)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+
     # ---- timed region
     sampler = ClockSampler(local)
     if world > 1:
@@ -313,20 +325,29 @@ def bench_gpu(args):
     sampler.start()
     time.sleep(0.3)
     t_wall0 = time.perf_counter()
-    per_step, stages = [], []
+    per_step = []
     for _ in range(args.steps):
         flush.fill_(1)
-        marks = step(ev=True)
-        stages.append(marks)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        per_step.append((e0, e1))
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
-    for marks in stages:
-        per_step.append(marks[0].elapsed_time(marks[-1]))
+    per_step = [a.elapsed_time(b) for a, b in per_step]
+    # per-stage times from eager steps with events between the stages
+    stages = []
+    for _ in range(3):
+        flush.fill_(1)
+        stages.append(step(ev=True))
+    torch.cuda.synchronize()
     names = ["build_neighbours", "classify_pca", "build_stencils (remap beside it)",
              "apply_ops", "backward (field adjoint beside it)"]
     stage_ms = {nm: statistics.mean(m[k].elapsed_time(m[k + 1]) for m in stages)
                 for k, nm in enumerate(names)}
+    eager_ms = statistics.mean(m[0].elapsed_time(m[-1]) for m in stages)
     total_ms = max_over_ranks(sum(per_step), dev, world)
     ms_step = total_ms / args.steps
     value = world * n / (ms_step * 1e-3)
@@ -577,8 +598,11 @@ def bench_gpu(args):
                        "step": "neighbours, detection, remap, stencils, apply, apply transpose"
                                + (", stencil adjoint" if have_bwd else ""),
                        "l2": "flushed (256 MB write) before every timed step",
+                       "launch": "the step captured once in a CUDA graph (both streams) and "
+                                 "replayed; stage_ms and ms_per_step_eager from eager steps",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "ms_per_step_eager": round(eager_ms, 4),
             "build_particles_per_s": round(n / ((stage_ms["build_neighbours"] +
                                                  stage_ms["classify_pca"] +
                                                  stage_ms["build_stencils (remap beside it)"])
