@@ -14,6 +14,9 @@
  *    col capacity, non-finite input, a remap needing more output rows) are
  *    recorded in the context's device status block: read it with
  *    mafp_get_status after the stream is done.
+ *  - Calls of one context must be ordered on the GPU (one stream, or streams
+ *    ordered by events): they share the context's scratch, so calls that
+ *    overlap on the GPU race on it.  Different contexts are independent.
  *  - Particle arrays are in the caller's order; all indices refer to it.
  *  - dtype selects the floating-point type of every "void*" real array of
  *    the call: float for MAFP_F32_REFINED / MAFP_F32_PLAIN, double for
@@ -32,7 +35,9 @@ extern "C" {
 #define MAFP_EINVAL (-1)     /* bad argument (null pointer, negative size, unknown dtype) */
 #define MAFP_ECAPACITY (-2)  /* a caller or context capacity is too small */
 #define MAFP_ECUDA (-3)      /* a CUDA runtime call failed (message in mafp_last_error) */
-#define MAFP_ETIMEOUT (-4)   /* a bounded device-side wait gave up */
+#define MAFP_ETIMEOUT (-4)   /* a bounded device-side wait gave up (status block); the
+                                waiting block then computed the value itself, so the
+                                outputs are exact but the call ran its slow path */
 #define MAFP_ENOTIMPL (-5)   /* entry point not implemented by this library */
 #define MAFP_ENONFINITE (-6) /* non-finite position or smoothing length seen on device */
 
@@ -68,6 +73,10 @@ typedef struct {
   double angle_band;     /* FP32 |n.w3| within this of cos(theta*) -> FP64 retake */
   double hfilm_band;     /* FP32 H_film within this relative band of h3D -> FP64 retake */
   double near_rel;       /* relative band for reporting near-threshold decisions (1e-6) */
+  double wait_limit;     /* polls of a bounded device-side wait (the one-pass scan's wait
+                            for an earlier tile) before it gives up and records
+                            MAFP_ETIMEOUT in the status block (2^22); no counterpart in
+                            the paper */
 } mafp_params;
 
 /* Launch shapes (no counterpart in the paper): lanes that cooperate on one

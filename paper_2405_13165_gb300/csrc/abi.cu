@@ -114,6 +114,7 @@ void mafp_default_params(mafp_params *p) {
   p->angle_band = 1e-3;
   p->hfilm_band = 1e-4;
   p->near_rel = 1e-6;
+  p->wait_limit = 4194304.0;
 }
 
 int mafp_create(mafp_ctx **out, const mafp_params *params, int64_t cap_particles,
@@ -153,6 +154,7 @@ int mafp_create(mafp_ctx **out, const mafp_params *params, int64_t cap_particles
       {(void **)&ctx->nbr_mask, sizeof(uint32_t) * kMaskWords * cap},
       {(void **)&ctx->overflow, sizeof(int32_t) * cap},
       {(void **)&ctx->scan_tmp, sizeof(long long) * (i64_len / 4096 + 4)},
+      {(void **)&ctx->scan_ctr, sizeof(int32_t) * 2},
       {(void **)&ctx->fallback, sizeof(int32_t) * cap},
       {(void **)&ctx->d_status, sizeof(DevStatus)},
       {(void **)&ctx->d_grid, sizeof(GridDev)},
@@ -173,7 +175,9 @@ int mafp_create(mafp_ctx **out, const mafp_params *params, int64_t cap_particles
     }
   }
   if (cudaMemset(ctx->d_status, 0, sizeof(DevStatus)) != cudaSuccess ||
-      cudaMemset(ctx->d_grid, 0, sizeof(GridDev)) != cudaSuccess) {
+      cudaMemset(ctx->d_grid, 0, sizeof(GridDev)) != cudaSuccess ||
+      cudaMemset(ctx->scan_tmp, 0, sizeof(long long) * (i64_len / 4096 + 4)) != cudaSuccess ||
+      cudaMemset(ctx->scan_ctr, 0, sizeof(int32_t) * 2) != cudaSuccess) {
     mafp_destroy(ctx);
     return MAFP_ECUDA;
   }
@@ -187,6 +191,7 @@ int mafp_destroy(mafp_ctx *ctx) {
   void *ptrs[] = {ctx->keys_a,    ctx->keys_b,   ctx->vals_a,       ctx->vals_b,
                   ctx->radix_hist, ctx->cell_start, ctx->cell_end,   ctx->spos,
                   ctx->ucell,     ctx->n_ucell,  ctx->counts,       ctx->scan_tmp,
+                  ctx->scan_ctr,
                   ctx->nbr_mask,  ctx->overflow,
                   ctx->fallback, ctx->d_status,  ctx->d_grid,
                   ctx->remap_i64, ctx->remap_i32, ctx->d_grids,   ctx->cell_base,

@@ -65,7 +65,8 @@ struct mafp_ctx {
   int32_t *counts;          // [cap] row lengths
   uint32_t *nbr_mask;       // [kMaskWords * cap] candidate hit bits, word-major
   int32_t *overflow;        // [cap] occupied cells whose candidates overflow the tile
-  long long *scan_tmp;      // [cap/1024 + 2]
+  long long *scan_tmp;      // tile states of the one-pass scan, zero between scans
+  int32_t *scan_ctr;        // [2] tickets and finished tiles of the scan, zero between scans
   int32_t *fallback;        // [cap] particles re-done in FP64
   mafp::DevStatus *d_status;
   mafp::GridDev *d_grid;     // all-clouds flag and totals

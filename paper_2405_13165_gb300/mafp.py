@@ -36,7 +36,7 @@ class MafpError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [(k, C.c_double) for k in
                 ("eps_lambda_max", "theta_star", "alpha_film", "alpha_w", "c_psi", "cond_fp64",
-                 "eps_band", "angle_band", "hfilm_band", "near_rel")]
+                 "eps_band", "angle_band", "hfilm_band", "near_rel", "wait_limit")]
 
 
 class Status(C.Structure):
