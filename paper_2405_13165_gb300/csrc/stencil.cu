@@ -125,6 +125,16 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
     for (int r = 0; r < M; ++r) bb[r] = rhs<M, C>(k, r);
     chol_solve_s<M, C>(Ls, invd, bb, lam[k]);
   }
+  // The Laplacian's refinement correction is kept apart (lamlo) instead of
+  // being added into lam: its solution has entries ~100x its coefficients on
+  // one-sided (free-surface, wall) rows, and rounding lam + d to FP32 would put
+  // back an error A * (rounding of lam) into the moment conditions, which the
+  // applied Laplacian sees divided by h.  Its coefficients are evaluated as
+  // w (p.lam + p.lamlo).
+  constexpr int KL = NR - 1;
+  C lamlo[M];
+#pragma unroll
+  for (int r = 0; r < M; ++r) lamlo[r] = C(0);
   if constexpr (REFINE) {
     // residual b - sum_j c_j p_j of the coefficients as they will be stored
     C R[VR];
@@ -176,7 +186,10 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
       for (int r = 0; r < M; ++r) rr[r] = rhs<M, C>(k, r) - sm[k * M + r];
       chol_solve_s<M, C>(Ls, invd, rr, d);
 #pragma unroll
-      for (int r = 0; r < M; ++r) lam[k][r] += d[r];
+      for (int r = 0; r < M; ++r) {
+        if (k == KL) lamlo[r] = d[r];
+        else lam[k][r] += d[r];
+      }
     }
     __syncwarp(gm);
   }
@@ -189,6 +202,12 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
       C s = 0;
 #pragma unroll
       for (int r = 0; r < M; ++r) s += p[r] * lam[k][r];
+      if (REFINE && k == KL) {
+        C sl = 0;
+#pragma unroll
+        for (int r = 0; r < M; ++r) sl += p[r] * lamlo[r];
+        s += sl;
+      }
       c[k] = w * s;
     }
     vec4_t<TS> out;
@@ -227,6 +246,12 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
         C s = 0;
 #pragma unroll
         for (int r = 0; r < M; ++r) s += p[r] * lam[k][r];
+        if (REFINE && k == KL) {
+          C sl = 0;
+#pragma unroll
+          for (int r = 0; r < M; ++r) sl += p[r] * lamlo[r];
+          s += sl;
+        }
         c[k] = w * s;
       }
       if constexpr (M == 10) {

@@ -111,3 +111,18 @@ def test_stencil_properties_on_all_rows(jet, gpu_run):
         model = torch.tensor(c.model, device="cuda")
         m3 = ok & (model == 0)
         assert torch.all((g[m3] - 1.0).abs() <= 1e-4), float((g[m3] - 1.0).abs().max())
+
+
+def test_outputs_on_all_rows(jet, gpu_run):
+    # every applied derivative of the cloud against the FP64 oracle (stencils
+    # and apply over all rows): the 1e-4 normwise bar and the componentwise
+    # p99 bar on each of the 16 columns (field x operator)
+    c, rp, col = jet
+    coef, status, _ = O.stencils(c.pos_h, c.model, rp, col)
+    out = O.apply(rp, col, coef, c.vp).reshape(-1, 16)
+    a = gpu_run["out"].reshape(-1, 16)
+    nw, p99 = column_error(a, out)
+    print("normwise per column:", np.array2string(nw, precision=2))
+    print("componentwise p99 per column:", np.array2string(p99, precision=2))
+    assert np.all(nw <= TOL[M.F32_REFINED]), nw
+    assert np.all(p99 <= P99_BAR[M.F32_REFINED]), p99
