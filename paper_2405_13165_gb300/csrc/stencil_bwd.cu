@@ -45,13 +45,19 @@ __device__ __forceinline__ void add_xyz<double>(double *p, double x, double y, d
 
 // neighbours a lane gathers ahead of use in the moment / lbar pass and the gradient pass
 constexpr int kGradGatherA = 2, kGradGatherC = 2;
+// ring depth of the streamed passes (entries in flight per lane)
+constexpr int kGradRing = 2;
 
 // Returns 0 done, 1 no gradient (deficient), 2 queued for the FP64 redo.
-template <typename TS, typename C, int M, int G, bool QUEUE>
+// RING (FP32 storage and arithmetic): the passes over the row stream the
+// neighbour records through the block's shared-memory ring (stream_row)
+// instead of gathering a few entries at a time into registers.
+template <typename TS, typename C, int M, int G, bool QUEUE, bool RING = false>
 __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *model,
                              const vec4_t<TS> *frame, const long long *row_ptr,
                              const int32_t *col, const vec4_t<TS> *fields,
-                             const vec4_t<TS> *gout, TS *gpos, const StParams<C> &sp, C *sm) {
+                             const vec4_t<TS> *gout, TS *gpos, const StParams<C> &sp, C *sm,
+                             float4 *ring = nullptr) {
   constexpr int NA = Basis<M>::NA, NR = Basis<M>::NR;
   constexpr int VA = pad_to(NA, G), VR = pad_to(NR * M, G);
   using V = vec4_t<TS>;
@@ -110,25 +116,30 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
 #pragma unroll
   for (int k = 0; k < 4 * M; ++k) Bf[k] = C(0);
   int cnt = 0;
-  for (long long e0 = b + lane; e0 < e1; e0 += kGradGatherA * G) {
-    V xs[kGradGatherA], fs[kGradGatherA];
-    int js[kGradGatherA];
-    bool oks[kGradGatherA];
-    gather_row_f<kGradGatherA, G>(e0, e1, i, mi, col, pos, model, fields, xs, fs, js, oks);
+  auto pass1 = [&](const V &xj, const V &fj, int, bool ok) {
+    C p[M];
+    C w = basis_at<M, C>(xi, ok ? xj : xi, hinv, t1, t2, sp, p);
+    w = ok ? w : C(0);   // other model / past the row end: contributes exact zeros
+    cnt += ok ? 1 : 0;
+    add_moments<M, C, VM>(A, w, p);
+    const V fv = ok ? fj : fi;
+    const C wdu[4] = {w * (C(fv.x) - C(fi.x)), w * (C(fv.y) - C(fi.y)),
+                      w * (C(fv.z) - C(fi.z)), w * (C(fv.w) - C(fi.w))};
 #pragma unroll
-    for (int u = 0; u < kGradGatherA; ++u) {
-      C p[M];
-      C w = basis_at<M, C>(xi, xs[u], hinv, t1, t2, sp, p);
-      w = oks[u] ? w : C(0);   // other model / past the row end: contributes exact zeros
-      cnt += oks[u] ? 1 : 0;
-      add_moments<M, C, VM>(A, w, p);
-      const V fj = fs[u];
-      const C wdu[4] = {w * (C(fj.x) - C(fi.x)), w * (C(fj.y) - C(fi.y)),
-                        w * (C(fj.z) - C(fi.z)), w * (C(fj.w) - C(fi.w))};
+    for (int f = 0; f < 4; ++f)
 #pragma unroll
-      for (int f = 0; f < 4; ++f)
+      for (int r = 0; r < M; ++r) Bf[f * M + r] += wdu[f] * p[r];
+  };
+  if constexpr (RING) {
+    stream_row<kGradRing, G, true>(b, e1, mi, col, pos, model, fields, ring, pass1);
+  } else {
+    for (long long e0 = b + lane; e0 < e1; e0 += kGradGatherA * G) {
+      V xs[kGradGatherA], fs[kGradGatherA];
+      int js[kGradGatherA];
+      bool oks[kGradGatherA];
+      gather_row_f<kGradGatherA, G>(e0, e1, i, mi, col, pos, model, fields, xs, fs, js, oks);
 #pragma unroll
-        for (int r = 0; r < M; ++r) Bf[f * M + r] += wdu[f] * p[r];
+      for (int u = 0; u < kGradGatherA; ++u) pass1(xs[u], fs[u], js[u], oks[u]);
     }
   }
 #pragma unroll
@@ -205,19 +216,11 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
   // film rows: sums of the frame coordinates (xi, eta, zeta) = y.(t1, t2, n) of
   // the neighbours and of their squares (the PCA's Rayleigh quotients)
   C sc[3] = {0, 0, 0}, sq[3] = {0, 0, 0};
-  for (long long e0 = b + lane; e0 < e1; e0 += kGradGatherC * G) {
-    V xs[kGradGatherC], fs[kGradGatherC];
-    int js[kGradGatherC];
-    bool oks[kGradGatherC];
-    gather_row_f<kGradGatherC, G>(e0, e1, i, mi, col, pos, model, fields, xs, fs, js, oks);
-#pragma unroll
-    for (int u = 0; u < kGradGatherC; ++u) {
-    const int j = js[u];
-    if (!oks[u] || j == i) continue;
-    const V xj = xs[u];
+  auto pass2 = [&](const V &xj, const V &fj, int j, bool ok) {
+    if (!ok || j == i) return;
     C p[M], gb[NR], g4[4];
     const C w = basis_at<M, C>(xi, xj, hinv, t1, t2, sp, p);
-    gbar(fs[u], gb, g4);
+    gbar(fj, gb, g4);
     const C dx = C(xj.x) - C(xi.x), dy = C(xj.y) - C(xi.y), dz = C(xj.z) - C(xi.z);
     const C s2 = ((dx * dx + dy * dy) + dz * dz) * (hinv * hinv);
     const C dws = s2 <= C(1) ? a2 * exp(-sp.alpha * s2) : C(0);
@@ -270,6 +273,17 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
     add_xyz<TS>(gpos + 4 * (int64_t)j, TS(d[0]), TS(d[1]), TS(d[2]));
 #pragma unroll
     for (int a = 0; a < 3; ++a) acc_i[a] -= d[a];
+  };
+  if constexpr (RING) {
+    stream_row<kGradRing, G, true>(b, e1, mi, col, pos, model, fields, ring, pass2);
+  } else {
+    for (long long e0 = b + lane; e0 < e1; e0 += kGradGatherC * G) {
+      V xs[kGradGatherC], fs[kGradGatherC];
+      int js[kGradGatherC];
+      bool oks[kGradGatherC];
+      gather_row_f<kGradGatherC, G>(e0, e1, i, mi, col, pos, model, fields, xs, fs, js, oks);
+#pragma unroll
+      for (int u = 0; u < kGradGatherC; ++u) pass2(xs[u], fs[u], js[u], oks[u]);
     }
   }
   if constexpr (M == 6) {
@@ -295,28 +309,33 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
 #pragma unroll
     for (int a = 0; a < 3; ++a) av[a] = (be1 * t1[a] + be2 * t2[a]) * hinv;
     const C bn1 = be1 * hinv, bn2 = be2 * hinv;
-    constexpr int U = 4;
-    for (long long e0 = b + lane; e0 < e1; e0 += U * G) {
-      V xs[U];
-      bool oks[U];
-      gather_row<U, G>(e0, e1, i, mi, col, pos, model, xs, oks);
+    auto pass3 = [&](const V &xj, const V &, int j, bool ok) {
+      if (!ok || j == i) return;
+      const C dx = C(xj.x) - C(xi.x), dy = C(xj.y) - C(xi.y), dz = C(xj.z) - C(xi.z);
+      const C zn = (dx * nv[0] + dy * nv[1] + dz * nv[2]) * hinv - zc;
+      const C z1 = (dx * t1[0] + dy * t1[1] + dz * t1[2]) * hinv - xc;
+      const C z2 = (dx * t2[0] + dy * t2[1] + dz * t2[2]) * hinv - ec;
+      const C tz = bn1 * z1 + bn2 * z2;
+      C d[3];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const long long e = e0 + (long long)u * G;
-        if (!oks[u]) continue;
-        const int j = col[e];
-        if (j == i) continue;
-        const C dx = C(xs[u].x) - C(xi.x), dy = C(xs[u].y) - C(xi.y), dz = C(xs[u].z) - C(xi.z);
-        const C zn = (dx * nv[0] + dy * nv[1] + dz * nv[2]) * hinv - zc;
-        const C z1 = (dx * t1[0] + dy * t1[1] + dz * t1[2]) * hinv - xc;
-        const C z2 = (dx * t2[0] + dy * t2[1] + dz * t2[2]) * hinv - ec;
-        const C tz = bn1 * z1 + bn2 * z2;
-        C d[3];
+      for (int a = 0; a < 3; ++a) d[a] = av[a] * zn + nv[a] * tz;
+      add_xyz<TS>(gpos + 4 * (int64_t)j, TS(d[0]), TS(d[1]), TS(d[2]));
 #pragma unroll
-        for (int a = 0; a < 3; ++a) d[a] = av[a] * zn + nv[a] * tz;
-        add_xyz<TS>(gpos + 4 * (int64_t)j, TS(d[0]), TS(d[1]), TS(d[2]));
+      for (int a = 0; a < 3; ++a) acc_i[a] -= d[a];
+    };
+    if constexpr (RING) {
+      stream_row<kGradRing, G, false>(b, e1, mi, col, pos, model, nullptr, ring, pass3);
+    } else {
+      constexpr int U = 4;
+      for (long long e0 = b + lane; e0 < e1; e0 += U * G) {
+        V xs[U];
+        bool oks[U];
+        gather_row<U, G>(e0, e1, i, mi, col, pos, model, xs, oks);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) acc_i[a] -= d[a];
+        for (int u = 0; u < U; ++u) {
+          const long long e = e0 + (long long)u * G;
+          pass3(xs[u], xs[u], oks[u] ? col[e] : -1, oks[u]);
+        }
       }
     }
   }
@@ -332,7 +351,14 @@ __global__ void __launch_bounds__(kStThreads, sizeof(C) == 4 ? (M == 10 ? 3 : 4)
     const long long *row_ptr, const int32_t *col, const vec4_t<TS> *fields,
     const vec4_t<TS> *gout, TS *gpos, StParams<C> sp, DevStatus *st, int32_t *queue) {
   constexpr int SMG = StSmem<M, G>::PER_GROUP;
+  // 3D rows stream their neighbours through a shared-memory ring (measured on
+  // the 1M jet cloud: 1.41 -> 1.34 ms with 2 entries in flight; 1.50 / 1.34 /
+  // 1.51 ms with 1 / 3 / 4).  Film rows keep the register gathers: with the
+  // ring their instance spills at its 128-register bound (0.55 -> 0.56-0.62 ms).
+  constexpr bool RING = sizeof(TS) == 4 && sizeof(C) == 4 && M == 10;
   __shared__ C smem[(kStThreads / G) * SMG];
+  // ring of the streamed passes: kGradRing slots x (position, field) per thread
+  __shared__ float4 ring[RING ? kGradRing * 2 * kStThreads : 1];
   C *sm = smem + (threadIdx.x / G) * SMG;
   const int lane = threadIdx.x & (G - 1);
   const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -340,8 +366,8 @@ __global__ void __launch_bounds__(kStThreads, sizeof(C) == 4 ? (M == 10 ? 3 : 4)
   const uint8_t want = M == 10 ? MAFP_MODEL_3D : MAFP_MODEL_2D;
   for (int64_t i = gid; i < n; i += ngroups) {
     if (model[i] != want) continue;
-    const int res = grad_particle<TS, C, M, G, QUEUE>(i, pos, model, frame, row_ptr, col, fields,
-                                                     gout, gpos, sp, sm);
+    const int res = grad_particle<TS, C, M, G, QUEUE, RING>(i, pos, model, frame, row_ptr, col,
+                                                           fields, gout, gpos, sp, sm, ring);
     if (res == 2 && lane == 0) queue[atomicAdd(&st->fallback_count, 1)] = (int32_t)i;
   }
 }

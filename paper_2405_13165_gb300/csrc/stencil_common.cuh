@@ -291,6 +291,86 @@ __device__ __forceinline__ void gather_row_f(long long e0, long long e1, int64_t
   for (int u = 0; u < U; ++u) ok[u] = (e0 + (long long)u * G < e1) && m[u] == mi;
 }
 
+// ---- software-pipelined row walk (FP32 storage) ---------------------------
+// A lane walks its entries e = b + lane + k G (k = 0, 1, ...) of row i.  The
+// neighbour records (position, and with FIELDS its field record) are copied by
+// cp.async into a ring of D slots in shared memory D entries before they are
+// used; the column index is loaded 2D entries before and the neighbour's model
+// byte D entries before (registers).  The dependent loads col -> pos / fields
+// then overlap the arithmetic of the entries in between instead of stalling at
+// every entry, and the records in flight hold no registers.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Slots of the block's ring: record r of slot s of thread t sits at
+// ((s * R + r) * kStThreads + t), so a warp's lanes touch consecutive 16-byte
+// words (no bank conflicts).  body(xj, fj, j, ok) runs once per entry of the
+// lane in row order; ok = the entry exists and j has the model of i (fj is xj
+// when !FIELDS; for !ok both may hold stale data and must not be used).
+template <int D, int G, bool FIELDS, typename F>
+__device__ __forceinline__ void stream_row(long long b, long long e1, uint8_t mi,
+                                           const int32_t *col, const float4 *pos,
+                                           const uint8_t *model, const float4 *fld,
+                                           float4 *ring, F &&body) {
+  constexpr int R = FIELDS ? 2 : 1;
+  const int t = threadIdx.x;
+  const int lane = t & (G - 1);
+  const int nloc = e1 > b + lane ? (int)((e1 - b - lane + G - 1) / G) : 0;
+  auto colk = [&](int k) -> int {
+    const long long e = b + lane + (long long)k * G;
+    return e < e1 ? col[e] : -1;
+  };
+  auto slot = [&](int s, int r) -> float4 * { return ring + (s * R + r) * kStThreads + t; };
+  int js[D], jn[D];
+  unsigned ms[D];
+#pragma unroll
+  for (int s = 0; s < D; ++s) js[s] = colk(s);
+#pragma unroll
+  for (int s = 0; s < D; ++s) {
+    ms[s] = 0xffu;
+    if (js[s] >= 0) {
+      ms[s] = model[js[s]];
+      cp_async16(slot(s, 0), pos + js[s]);
+      if constexpr (FIELDS) cp_async16(slot(s, 1), fld + js[s]);
+    }
+    cp_async_commit();
+  }
+#pragma unroll
+  for (int s = 0; s < D; ++s) jn[s] = colk(D + s);
+  for (int k0 = 0; k0 < nloc; k0 += D) {
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+      cp_async_wait<D - 1>();   // the oldest group: this slot's records
+      const float4 xj = *slot(s, 0);
+      float4 fj = xj;
+      if constexpr (FIELDS) fj = *slot(s, 1);
+      const int j = js[s];
+      body(xj, fj, j, j >= 0 && ms[s] == (unsigned)mi);
+      // refill the slot (its records are consumed) with the entry D further on
+      const int jx = jn[s];
+      js[s] = jx;
+      ms[s] = 0xffu;
+      if (jx >= 0) {
+        ms[s] = model[jx];
+        cp_async16(slot(s, 0), pos + jx);
+        if constexpr (FIELDS) cp_async16(slot(s, 1), fld + jx);
+      }
+      cp_async_commit();
+      jn[s] = colk(k0 + s + 2 * D);
+    }
+  }
+  cp_async_wait<0>();
+}
+
 template <int M, int G>
 struct StSmem {
   static constexpr int NA = Basis<M>::NA, NR = Basis<M>::NR;
