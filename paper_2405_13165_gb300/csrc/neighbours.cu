@@ -480,25 +480,45 @@ __global__ void k_check_nnz(const long long *row_ptr, int64_t n, long long cap_n
   if (nnz > cap_nnz) set_error(st, MAFP_ECAPACITY, nnz);
 }
 
-// ------------------------------------------- thread-per-particle mask path
+// ------------------------------------------------ warp-per-cell mask path
 // Every particle of a cell shares the candidate set "27 cells around it",
 // which is 9 runs of consecutive sorted positions (3 x-adjacent cells each).
-// The mask kernel stages that set in shared memory once per cell; each thread
-// (one particle) tests all candidates against itself reading them as shared
-// memory broadcasts, and writes one bit per candidate (word-major layout
-// mask[w * stride + p], coalesced across the block) plus its row length.
-// The fill kernel turns the bits back into column indices, so the distance
-// tests run once.
+// Each warp takes occupied cells from a device work queue (an atomic ticket
+// per cell) and handles its cell alone, with warp-level synchronisation only:
+// a film cell (a dozen particles, ~4 candidate words) and a 3D cell (~40
+// particles, ~37 words) then cost the warp in proportion to their work, and
+// no block waits at a barrier for its slowest thread.  The candidates are
+// staged in windows of kWinWords words (32 candidates each) in the warp's part
+// of shared memory; the warp's lanes take (word, particle) items of the window
+// (consecutive lanes, consecutive particles of one word: the candidate reads
+// are broadcasts), test 32 candidates against the particle and write one bit
+// per candidate (word-major mask[w * stride + p], coalesced) plus the row
+// length.  The fill kernel turns the bits back into column indices, so the
+// distance tests run once.
 constexpr int kMaskThreads = 128;
-constexpr int kMaskTile = kMaskCap + kMaskWords;   // candidates plus one pad per word
-// FP32 tile as four arrays (x, y, z, h/2), two pad floats per word of 32
-// candidates: a float2 read gives two consecutive candidates, and the words
-// that the threads of one warp test sit in different banks
-constexpr int kMaskTileSoA = kMaskCap + 2 * kMaskWords;
-constexpr int kMaskMaxP = 512;                     // particles of one cell in the mask kernel
+constexpr int kMaskWarps = kMaskThreads / 32;
+constexpr int kMaskMaxP = 256;   // particles of one cell in the mask kernel (else: overflow path)
 static_assert(kMaskCap < 65536 && kMaskMaxP % 2 == 0, "two 16-bit hit counts per word");
+// FP32 window: four arrays (x, y, z, h/2) of kWinWords words, two pad floats
+// per word: a float2 read gives two consecutive candidates, and the words that
+// lanes of one warp test sit in different banks.  FP64: double4 records, one
+// pad record per word.
+template <typename T> struct MaskWin;
+template <> struct MaskWin<float> {
+  static constexpr int WORDS = 11;
+  static constexpr int SOA = 32 * WORDS + 2 * WORDS;   // floats per array
+  static constexpr int TILE_BYTES = 4 * SOA * (int)sizeof(float);
+};
+template <> struct MaskWin<double> {
+  static constexpr int WORDS = 5;
+  static constexpr int TILE_BYTES = (32 * WORDS + WORDS) * (int)sizeof(double4_16a);
+};
+template <typename T>
+constexpr int kMaskWarpBytes = MaskWin<T>::TILE_BYTES + (kMaskMaxP / 2) * (int)sizeof(unsigned);
+
 constexpr int kFillThreads = 256;
-constexpr int kFillChunk = 64;            // particles of a cell expanded per round
+constexpr int kFillWarps = kFillThreads / 32;
+constexpr int kFillWinWords = 16;   // candidate words of one fill window
 
 // Rows of the 27-cell neighbourhood of global cell `key`: run r (dz = r/3-1,
 // dy = r%3-1) covers cells key-1..key+1 of that (y, z) row of the key's own
@@ -529,6 +549,39 @@ __device__ __forceinline__ void cell_runs(int key, const CloudGrids &cg,
   *len_out = hi > lo ? hi - lo : 0;
 }
 
+// The 9 runs of a cell, one per lane 0..8 (start, length, offset in the
+// cell's candidate list), and the candidate total (every lane).
+__device__ __forceinline__ void warp_cell_runs(int key, const CloudGrids &cg,
+                                               const int32_t *cell_start,
+                                               const int32_t *cell_end, int lane, int *lo,
+                                               int *len, int *off, int *total) {
+  *lo = 0;
+  *len = 0;
+  if (lane < 9) cell_runs(key, cg, cell_start, cell_end, lane, lo, len);
+  int inc = *len;
+#pragma unroll
+  for (int o = 1; o < 16; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  *off = inc - *len;
+  *total = __shfl_sync(0xffffffffu, inc, 8);
+}
+
+// Calls put(c - c0, sorted position of candidate c) for every candidate c of
+// the window [c0, c1), lanes striding over each run's part of the window.
+template <typename F>
+__device__ __forceinline__ void for_window(int lo, int len, int off, int c0, int c1, int lane,
+                                           F &&put) {
+#pragma unroll 1
+  for (int r = 0; r < 9; ++r) {
+    const int rlo = __shfl_sync(0xffffffffu, lo, r), rlen = __shfl_sync(0xffffffffu, len, r);
+    const int roff = __shfl_sync(0xffffffffu, off, r);
+    const int a = max(c0, roff), b = min(c1, roff + rlen);
+    for (int c = a + lane; c < b; c += 32) put(c - c0, rlo + (c - roff));
+  }
+}
+
 // FP32 test with an explicit band: certainly in / certainly out from FP32,
 // the FP64 definition inside +-1e-5 of the bound.
 __device__ __forceinline__ bool support_test(const float4 &a, const float4 &b) {
@@ -550,84 +603,74 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
     const int32_t *svals, const int32_t *cell_start, const int32_t *cell_end, int32_t *counts,
     uint32_t *mask, int64_t stride, int32_t *overflow, int32_t *n_overflow) {
   using V = vec4_t<T>;
+  constexpr int WW = MaskWin<T>::WORDS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V *cand = reinterpret_cast<V *>(smem_raw);
-  float *tx = reinterpret_cast<float *>(smem_raw), *ty = tx + kMaskTileSoA,
-        *tz = ty + kMaskTileSoA, *th = tz + kMaskTileSoA;
-  __shared__ int r_lo[9], r_len[9], r_off[10];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  unsigned char *mine = smem_raw + wp * kMaskWarpBytes<T>;
+  V *cand = reinterpret_cast<V *>(mine);
+  float *tx = reinterpret_cast<float *>(mine);
+  float *ty = tx + (sizeof(T) == 4 ? MaskWin<float>::SOA : 0);
+  float *tz = ty + (sizeof(T) == 4 ? MaskWin<float>::SOA : 0);
+  float *th = tz + (sizeof(T) == 4 ? MaskWin<float>::SOA : 0);
   // per-particle hit counts, two 16-bit counts per word (a row has at most
-  // kMaskCap < 65536 candidates), so the FP32 tile and these fit 8 blocks per SM
-  __shared__ unsigned cnt_s[kMaskMaxP / 2];
-  __shared__ int s_ovf, s_cb;
+  // kMaskCap < 65536 candidates)
+  unsigned *cnt = reinterpret_cast<unsigned *>(mine + MaskWin<T>::TILE_BYTES);
   if (!cg.all->ok) return;
-  const int tid = threadIdx.x;
   const int nu = n_ucell[0];
   for (;;) {
-    // cells are handed out one at a time (work ticket n_ucell[2]): a block that
+    // cells are handed out one at a time (work ticket n_ucell[2]): a warp that
     // finishes a light film cell takes the next cell at once
-    if (tid == 0) s_cb = atomicAdd(n_ucell + 2, 1);
-    __syncthreads();
-    const int cb = s_cb;
+    int cb = 0;
+    if (lane == 0) cb = atomicAdd(n_ucell + 2, 1);
+    cb = __shfl_sync(0xffffffffu, cb, 0);
     if (cb >= nu) break;
     const int key = ucell[2 * cb], s0 = ucell[2 * cb + 1];
-    const int s1 = cell_end[key];
-    if (tid < 9) cell_runs(key, cg, cell_start, cell_end, tid, &r_lo[tid], &r_len[tid]);
-    __syncthreads();
-    if (tid == 0) {
-      int o = 0;
-      for (int r = 0; r < 9; ++r) {
-        r_off[r] = o;
-        o += r_len[r];
-      }
-      r_off[9] = o;
-      // too many candidates for the tile, or too many particles for the
-      // per-particle counters: the warp-per-particle kernel takes the cell
-      s_ovf = (o > kMaskCap || s1 - s0 > kMaskMaxP) ? 1 : 0;
-      if (s_ovf) overflow[atomicAdd(n_overflow, 1)] = cb;
+    const int P = cell_end[key] - s0;
+    int lo, len, off, total;
+    warp_cell_runs(key, cg, cell_start, cell_end, lane, &lo, &len, &off, &total);
+    if (total > kMaskCap || P > kMaskMaxP) {
+      // too many candidates for the mask words, or particles for the counters:
+      // the warp-per-particle kernel takes the cell
+      if (lane == 0) overflow[atomicAdd(n_overflow, 1)] = cb;
+      continue;
     }
-    __syncthreads();
-    const int total = r_off[9];
-    if (!s_ovf) {
-      // the tile holds candidate c at slot c + c / 32: one pad entry per word
-      // puts the words that different threads test in different banks
-      // (FP32: slot c + 2 (c / 32) of four arrays, h halved)
-      for (int r = 0; r < 9; ++r)
-        for (int t = tid; t < r_len[r]; t += kMaskThreads) {
-          const int c = r_off[r] + t;
-          const V v = ld4(spos + r_lo[r] + t);
-          if constexpr (sizeof(T) == 4) {
-            const int sl = c + 2 * (c >> 5);
-            tx[sl] = v.x;
-            ty[sl] = v.y;
-            tz[sl] = v.z;
-            th[sl] = 0.5f * v.w;   // exact: r = h_i / 2 + h_j / 2 = (h_i + h_j) / 2
-          } else {
-            cand[c + (c >> 5)] = v;
-          }
+    for (int q = lane; q < (P + 1) / 2; q += 32) cnt[q] = 0u;
+    const int nwords = (total + 31) >> 5;
+    for (int w0 = 0; w0 < nwords; w0 += WW) {
+      const int w1 = min(nwords, w0 + WW);
+      __syncwarp();   // the previous window's reads are done
+      for_window(lo, len, off, w0 * 32, min(total, w1 * 32), lane, [&](int c, int sp) {
+        const V v = ld4(spos + sp);
+        if constexpr (sizeof(T) == 4) {
+          const int sl = c + 2 * (c >> 5);
+          tx[sl] = v.x;
+          ty[sl] = v.y;
+          tz[sl] = v.z;
+          th[sl] = 0.5f * v.w;   // exact: r = h_i / 2 + h_j / 2 = (h_i + h_j) / 2
+        } else {
+          cand[c + (c >> 5)] = v;
         }
-      const int P = s1 - s0;
-      for (int q = tid; q < (P + 1) / 2; q += kMaskThreads) cnt_s[q] = 0u;
-      __syncthreads();
-      const int nwords = (total + 31) >> 5;
-      const int own = r_off[4] + (s0 - r_lo[4]);   // the cell's own particles, in run 4
-      // one work item = (word, particle); consecutive threads take consecutive
-      // particles of a word, so small cells still fill the block
-      const int items = P * nwords;
-      for (int it = tid; it < items; it += kMaskThreads) {
-        const int w = it / P, q = it - w * P;
-        const int oc = own + q;
+      });
+      __syncwarp();
+      // one work item = (word, particle); consecutive lanes take consecutive
+      // particles of a word, so small cells still fill the warp
+      const int items = P * (w1 - w0);
+      for (int it = lane; it < items; it += 32) {
+        const int wl = it / P, q = it - wl * P;
+        const int w = w0 + wl;
         const int base = w << 5;
         const uint32_t valid = (total - base) >= 32 ? 0xffffffffu : ((1u << (total - base)) - 1u);
+        const V xi = ld4(spos + s0 + q);
         uint32_t m = 0, band = 0;
         if constexpr (sizeof(T) == 4) {
-          // two candidates per packed FP32 instruction; the tile always holds
-          // 32 * nwords <= kMaskCap slots (plus pads), so reads past `total`
-          // stay in it and are masked off
-          const int so = oc + 2 * (oc >> 5);
-          const float2 nx = make_float2(-tx[so], -tx[so]), ny = make_float2(-ty[so], -ty[so]);
-          const float2 nz = make_float2(-tz[so], -tz[so]), hh = make_float2(th[so], th[so]);
+          // two candidates per packed FP32 instruction; the window always
+          // holds 32 * WW slots (plus pads), so reads past `total` stay in it
+          // and are masked off
+          const float hi2 = 0.5f * xi.w;
+          const float2 nx = make_float2(-xi.x, -xi.x), ny = make_float2(-xi.y, -xi.y);
+          const float2 nz = make_float2(-xi.z, -xi.z), hh = make_float2(hi2, hi2);
           const float2 klo = make_float2(0.99999f, 0.99999f), khi = make_float2(1.00001f, 1.00001f);
-          const int sb = base + 2 * w;   // slot of candidate 32 w
+          const int sb = 34 * wl;   // slot of candidate 32 w in the window
 #pragma unroll
           for (int k = 0; k < 32; k += 2) {
             const float2 bx = *reinterpret_cast<const float2 *>(tx + sb + k);
@@ -640,11 +683,11 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
             d2 = __ffma2_rn(dz, dz, d2);
             const float2 r = __fadd2_rn(bh, hh);
             const float2 r2 = __fmul2_rn(r, r);
-            const float2 lo = __fmul2_rn(r2, klo), hi = __fmul2_rn(r2, khi);
-            m |= (d2.x < lo.x ? 1u : 0u) << k;
-            m |= (d2.y < lo.y ? 1u : 0u) << (k + 1);
-            band |= (d2.x <= hi.x ? 1u : 0u) << k;
-            band |= (d2.y <= hi.y ? 1u : 0u) << (k + 1);
+            const float2 l2 = __fmul2_rn(r2, klo), h2 = __fmul2_rn(r2, khi);
+            m |= (d2.x < l2.x ? 1u : 0u) << k;
+            m |= (d2.y < l2.y ? 1u : 0u) << (k + 1);
+            band |= (d2.x <= h2.x ? 1u : 0u) << k;
+            band |= (d2.y <= h2.y ? 1u : 0u) << (k + 1);
           }
           m &= valid;
           band &= valid & ~m;
@@ -653,97 +696,83 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
             const int k = __ffs(band) - 1;
             band &= band - 1;
             const int sl = sb + k;
-            if (in_support64(-nx.x, -ny.x, -nz.x, 2.0f * hh.x, tx[sl], ty[sl], tz[sl], 2.0f * th[sl]))
+            if (in_support64(xi.x, xi.y, xi.z, xi.w, tx[sl], ty[sl], tz[sl], 2.0f * th[sl]))
               m |= 1u << k;
           }
         } else {
-          const V xi = cand[oc + (oc >> 5)];
-          const V *cw = cand + base + w;           // slot of candidate 32 w
+          const V *cw = cand + 33 * wl;   // slot of candidate 32 w in the window
           for (int k = 0; k < 32; ++k)
             if ((valid >> k) & 1u)
               if (support_test(xi, cw[k])) m |= 1u << k;
         }
         mask[(int64_t)w * stride + s0 + q] = m;
-        atomicAdd(&cnt_s[q >> 1], (unsigned)__popc(m) << ((q & 1) * 16));
+        atomicAdd(&cnt[q >> 1], (unsigned)__popc(m) << ((q & 1) * 16));
       }
-      __syncthreads();
-      for (int q = tid; q < P; q += kMaskThreads)
-        counts[svals[s0 + q]] = (int)((cnt_s[q >> 1] >> ((q & 1) * 16)) & 0xffffu);
     }
-    __syncthreads();
+    __syncwarp();
+    for (int q = lane; q < P; q += 32)
+      counts[svals[s0 + q]] = (int)((cnt[q >> 1] >> ((q & 1) * 16)) & 0xffffu);
+    __syncwarp();   // the counters are read before the next cell clears them
   }
 }
 
-// Fill pass for the mask kernel's cells: one block per occupied cell, the
-// cell's particles in chunks of kFillChunk.  Staging (candidate indices, the
-// chunk's hit words and row starts) is done by the whole block with
-// independent loads, so the expansion itself reads only shared memory: one
-// warp per particle, one candidate per lane, ballot compaction into the row
-// with coalesced stores.  Rows come out ascending when the cloud is in cell
-// order (candidates are runs of consecutive sorted positions, ascending).
+// Fill pass for the mask kernel's cells, also one warp per cell from a work
+// queue.  The cell's particles go in chunks of 32 (lane = particle, its row
+// start and running length in registers); for each window of kFillWinWords
+// candidate words the warp stages the candidates' original indices and the
+// chunk's hit words (coalesced) in its part of shared memory, then expands the
+// chunk's rows one particle at a time: one candidate per lane, ballot-free
+// compaction by popcount into the row, coalesced stores.  Rows come out
+// ascending when the cloud is in cell order (candidates are runs of
+// consecutive sorted positions, ascending).
 __global__ void __launch_bounds__(kFillThreads) k_nbr_fill(
     CloudGrids cg, const int32_t *ucell, int32_t *n_ucell, const int32_t *svals,
     const int32_t *cell_start, const int32_t *cell_end, const uint32_t *mask, int64_t stride,
     const long long *row_ptr, int32_t *col, long long cap_nnz, int64_t n) {
-  __shared__ int r_lo[9], r_len[9], r_off[10];
-  __shared__ uint32_t mw[kMaskWords][kFillChunk];
-  __shared__ int32_t cand_v[kMaskCap];   // original index of every candidate of the cell
-  __shared__ long long rs[kFillChunk];   // row starts of the chunk's particles
-  __shared__ int s_cb;
+  __shared__ int32_t cand_v[kFillWarps][kFillWinWords * 32];   // original indices
+  __shared__ uint32_t mw[kFillWarps][kFillWinWords][32];       // hit words of the chunk
   if (!cg.all->ok) return;
   if (row_ptr[n] > cap_nnz) return;
-  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
+  int32_t *cv = cand_v[wp];
   const int nu = n_ucell[0];
   for (;;) {
-    if (tid == 0) s_cb = atomicAdd(n_ucell + 3, 1);   // work ticket, as in the mask kernel
-    __syncthreads();
-    const int cb = s_cb;
+    int cb = 0;
+    if (lane == 0) cb = atomicAdd(n_ucell + 3, 1);   // work ticket, as in the mask kernel
+    cb = __shfl_sync(0xffffffffu, cb, 0);
     if (cb >= nu) break;
     const int key = ucell[2 * cb], s0 = ucell[2 * cb + 1];
-    const int s1 = cell_end[key];
-    if (tid < 9) cell_runs(key, cg, cell_start, cell_end, tid, &r_lo[tid], &r_len[tid]);
-    __syncthreads();
-    if (tid < 32) {
-      // exclusive prefix of the 9 run lengths (lanes 0..8), shuffles only
-      const int v = tid < 9 ? r_len[tid] : 0;
-      int inc = v;
-#pragma unroll
-      for (int o = 1; o < 16; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, inc, o);
-        if (tid >= o) inc += u;
-      }
-      if (tid < 9) r_off[tid] = inc - v;
-      if (tid == 8) r_off[9] = inc;
-    }
-    __syncthreads();
-    const int total = r_off[9];
-    const int P = s1 - s0;
-    if (total <= kMaskCap && P <= kMaskMaxP) {   // the mask kernel's cells
-      for (int r = 0; r < 9; ++r)
-        for (int t = tid; t < r_len[r]; t += kFillThreads) cand_v[r_off[r] + t] = svals[r_lo[r] + t];
-      const int nwords = (total + 31) >> 5;
-      for (int p0 = 0; p0 < P; p0 += kFillChunk) {
-        const int np = min(kFillChunk, P - p0);
-        for (int k = tid; k < nwords * kFillChunk; k += kFillThreads) {
-          const int w = k / kFillChunk, q = k % kFillChunk;
-          mw[w][q] = q < np ? mask[(int64_t)w * stride + s0 + p0 + q] : 0u;
-        }
-        for (int q = tid; q < np; q += kFillThreads) rs[q] = row_ptr[svals[s0 + p0 + q]];
-        __syncthreads();
-        for (int q = wp; q < np; q += kFillThreads / 32) {
-          int32_t *crow = col + rs[q];
-          int at = 0;
-          for (int w = 0; w < nwords; ++w) {
-            const uint32_t word = mw[w][q];
-            if ((word >> lane) & 1u) crow[at + __popc(word & lt)] = cand_v[(w << 5) + lane];
-            at += __popc(word);
+    const int P = cell_end[key] - s0;
+    int lo, len, off, total;
+    warp_cell_runs(key, cg, cell_start, cell_end, lane, &lo, &len, &off, &total);
+    if (total > kMaskCap || P > kMaskMaxP) continue;   // the overflow path fills it
+    const int nwords = (total + 31) >> 5;
+    for (int p0 = 0; p0 < P; p0 += 32) {
+      const int np = min(32, P - p0);
+      const int q = p0 + lane;
+      const long long rs = lane < np ? row_ptr[svals[s0 + q]] : 0;
+      int at = 0;
+      for (int w0 = 0; w0 < nwords; w0 += kFillWinWords) {
+        const int w1 = min(nwords, w0 + kFillWinWords);
+        __syncwarp();   // the previous window's reads are done
+        for_window(lo, len, off, w0 * 32, min(total, w1 * 32), lane,
+                   [&](int c, int sp) { cv[c] = svals[sp]; });
+        for (int w = w0; w < w1; ++w)
+          mw[wp][w - w0][lane] = lane < np ? mask[(int64_t)w * stride + s0 + q] : 0u;
+        __syncwarp();
+        for (int k = 0; k < np; ++k) {
+          int32_t *crow = col + __shfl_sync(0xffffffffu, rs, k);
+          int a = __shfl_sync(0xffffffffu, at, k);
+          for (int w = w0; w < w1; ++w) {
+            const uint32_t word = mw[wp][w - w0][k];
+            if ((word >> lane) & 1u) crow[a + __popc(word & lt)] = cv[(w - w0) * 32 + lane];
+            a += __popc(word);
           }
+          if (lane == k) at = a;
         }
-        __syncthreads();
       }
     }
-    __syncthreads();
   }
 }
 
@@ -896,9 +925,7 @@ static int build_neighbours_t(mafp_ctx *ctx, int64_t n, int nb, const long long 
   int32_t *n_overflow = ctx->n_ucell + 1;
   const int64_t stride = ctx->cap_particles;
   MAFP_TIMED(ctx, s, sizeof(T) == 4 ? "k_nbr_mask<float>" : "k_nbr_mask<double>",
-             k_nbr_mask<T><<<sms * 16, kMaskThreads,
-                             sizeof(T) == 4 ? 4 * kMaskTileSoA * sizeof(float) : kMaskTile * sizeof(V),
-                             s>>>(
+             k_nbr_mask<T><<<sms * 16, kMaskThreads, kMaskWarps * kMaskWarpBytes<T>, s>>>(
                  cg, ctx->ucell, ctx->n_ucell, spos, vin, ctx->cell_start,
                  ctx->cell_end, ctx->counts, ctx->nbr_mask, stride, ctx->overflow, n_overflow));
   MAFP_TIMED(ctx, s, "k_nbr<T,false>(overflow cells)",
@@ -963,9 +990,9 @@ int build_neighbours_batched(mafp_ctx *ctx, int64_t n, int32_t dtype, int32_t nc
 
 void init_kernel_attributes() {
   cudaFuncSetAttribute(k_nbr_mask<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       4 * kMaskTileSoA * (int)sizeof(float));
+                       kMaskWarps * kMaskWarpBytes<float>);
   cudaFuncSetAttribute(k_nbr_mask<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kMaskTile * (int)sizeof(double4_16a));
+                       kMaskWarps * kMaskWarpBytes<double>);
   cudaFuncSetAttribute(k_nbr<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kNbrSmemBytes);
   cudaFuncSetAttribute(k_nbr<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
