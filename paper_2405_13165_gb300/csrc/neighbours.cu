@@ -516,7 +516,7 @@ template <> struct MaskWin<double> {
 template <typename T>
 constexpr int kMaskWarpBytes = MaskWin<T>::TILE_BYTES + (kMaskMaxP / 2) * (int)sizeof(unsigned);
 
-constexpr int kFillThreads = 256;
+constexpr int kFillThreads = 128;
 constexpr int kFillWarps = kFillThreads / 32;
 constexpr int kFillWinWords = 16;   // candidate words of one fill window
 
