@@ -149,7 +149,7 @@ int mafp_create(mafp_ctx **out, const mafp_params *params, int64_t cap_particles
       {(void **)&ctx->cell_end, sizeof(int32_t) * cap_cells},
       {(void **)&ctx->spos, (size_t)(32 * cap)},
       {(void **)&ctx->ucell, sizeof(int32_t) * 2 * cap},
-      {(void **)&ctx->n_ucell, sizeof(int32_t) * 4},
+      {(void **)&ctx->n_ucell, sizeof(int32_t) * 8},
       {(void **)&ctx->counts, sizeof(int32_t) * cap},
       {(void **)&ctx->nbr_mask, sizeof(uint32_t) * kMaskWords * cap},
       {(void **)&ctx->overflow, sizeof(int32_t) * cap},

@@ -60,8 +60,9 @@ struct mafp_ctx {
   int32_t *radix_hist;      // [256 * max_tiles] (+1 for the scan total)
   int32_t *cell_start, *cell_end;
   void *spos;               // sorted positions, 32 bytes per particle
-  int32_t *ucell;           // [3 * cap] nonempty cells: key, start, end
-  int32_t *n_ucell;         // device counter
+  int32_t *ucell;           // [2 * cap] occupied cells: key, first sorted position
+  int32_t *n_ucell;         // device counters: cells (front group), overflow cells, mask and
+                            // fill tickets, cells (back group)
   int32_t *counts;          // [cap] row lengths
   uint32_t *nbr_mask;       // [kMaskWords * cap] candidate hit bits, word-major
   int32_t *overflow;        // [cap] occupied cells whose candidates overflow the tile

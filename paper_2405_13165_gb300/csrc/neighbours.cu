@@ -271,7 +271,8 @@ __global__ void k_clear_cells(const GridDev *g, int32_t *cell_start, int32_t *ce
   if (!g->ok) return;
   const long long nc = g->ncells;
   // occupied cells, overflow cells, and the work tickets of the mask and fill kernels
-  if (blockIdx.x == 0 && threadIdx.x == 0) n_ucell[0] = n_ucell[1] = n_ucell[2] = n_ucell[3] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    n_ucell[0] = n_ucell[1] = n_ucell[2] = n_ucell[3] = n_ucell[4] = 0;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nc;
        k += (long long)gridDim.x * blockDim.x) {
     cell_start[k] = INT_MAX;
@@ -345,6 +346,15 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
 
 // Exclusive scan of the (digit-major) histogram; reuses the int32->int64 scan.
 // --------------------------------------------------------- cell ranges
+// Occupied cells go to the work queue in two groups, the ones holding at least
+// kBigCell particles (3D cells at the usual h / dx) ahead of the rest, so the
+// costly cells are taken first and the kernels end on cheap ones.
+constexpr int kBigCell = 24;
+// Slot of the cell with ticket t: the first n_ucell[0] tickets are the front
+// group, the n_ucell[4] after them the back group (stored from slot n - 1 down).
+__device__ __forceinline__ int cell_slot(int t, int nbig, int64_t n) {
+  return t < nbig ? t : (int)(n - 1 - (t - nbig));
+}
 template <typename T>
 __global__ void k_cells(const uint32_t *skeys, const int32_t *svals, int64_t n,
                         const vec4_t<T> *pos, vec4_t<T> *spos, int32_t *cell_start,
@@ -360,7 +370,12 @@ __global__ void k_cells(const uint32_t *skeys, const int32_t *svals, int64_t n,
     if (i != (int32_t)s) st->not_identity = 1;
     if (s == 0 || skeys[s - 1] != key) {
       cell_start[key] = (int32_t)s;
-      int u = atomicAdd(n_ucell, 1);
+      // the work queue of the mask and fill kernels, costly cells first: cells
+      // of at least kBigCell particles fill the list from the front, the others
+      // from the back (slot n - 1 - u; there are at most n cells)
+      const bool big = s + kBigCell - 1 < n && skeys[s + kBigCell - 1] == key;
+      const int64_t u = big ? (int64_t)atomicAdd(n_ucell, 1)
+                            : n - 1 - (int64_t)atomicAdd(n_ucell + 4, 1);
       ucell[2 * u] = (int32_t)key;
       ucell[2 * u + 1] = (int32_t)s;
     }
@@ -601,7 +616,7 @@ template <typename T>
 __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
     CloudGrids cg, const int32_t *ucell, int32_t *n_ucell, const vec4_t<T> *spos,
     const int32_t *svals, const int32_t *cell_start, const int32_t *cell_end, int32_t *counts,
-    uint32_t *mask, int64_t stride, int32_t *overflow, int32_t *n_overflow) {
+    uint32_t *mask, int64_t stride, int32_t *overflow, int32_t *n_overflow, int64_t n) {
   using V = vec4_t<T>;
   constexpr int WW = MaskWin<T>::WORDS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -616,14 +631,15 @@ __global__ void __launch_bounds__(kMaskThreads) k_nbr_mask(
   // kMaskCap < 65536 candidates)
   unsigned *cnt = reinterpret_cast<unsigned *>(mine + MaskWin<T>::TILE_BYTES);
   if (!cg.all->ok) return;
-  const int nu = n_ucell[0];
+  const int nbig = n_ucell[0], nu = nbig + n_ucell[4];
   for (;;) {
     // cells are handed out one at a time (work ticket n_ucell[2]): a warp that
     // finishes a light film cell takes the next cell at once
-    int cb = 0;
-    if (lane == 0) cb = atomicAdd(n_ucell + 2, 1);
-    cb = __shfl_sync(0xffffffffu, cb, 0);
-    if (cb >= nu) break;
+    int t = 0;
+    if (lane == 0) t = atomicAdd(n_ucell + 2, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= nu) break;
+    const int cb = cell_slot(t, nbig, n);
     const int key = ucell[2 * cb], s0 = ucell[2 * cb + 1];
     const int P = cell_end[key] - s0;
     int lo, len, off, total;
@@ -736,12 +752,13 @@ __global__ void __launch_bounds__(kFillThreads) k_nbr_fill(
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   int32_t *cv = cand_v[wp];
-  const int nu = n_ucell[0];
+  const int nbig = n_ucell[0], nu = nbig + n_ucell[4];
   for (;;) {
-    int cb = 0;
-    if (lane == 0) cb = atomicAdd(n_ucell + 3, 1);   // work ticket, as in the mask kernel
-    cb = __shfl_sync(0xffffffffu, cb, 0);
-    if (cb >= nu) break;
+    int t = 0;
+    if (lane == 0) t = atomicAdd(n_ucell + 3, 1);   // work ticket, as in the mask kernel
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= nu) break;
+    const int cb = cell_slot(t, nbig, n);
     const int key = ucell[2 * cb], s0 = ucell[2 * cb + 1];
     const int P = cell_end[key] - s0;
     int lo, len, off, total;
@@ -927,7 +944,8 @@ static int build_neighbours_t(mafp_ctx *ctx, int64_t n, int nb, const long long 
   MAFP_TIMED(ctx, s, sizeof(T) == 4 ? "k_nbr_mask<float>" : "k_nbr_mask<double>",
              k_nbr_mask<T><<<sms * 16, kMaskThreads, kMaskWarps * kMaskWarpBytes<T>, s>>>(
                  cg, ctx->ucell, ctx->n_ucell, spos, vin, ctx->cell_start,
-                 ctx->cell_end, ctx->counts, ctx->nbr_mask, stride, ctx->overflow, n_overflow));
+                 ctx->cell_end, ctx->counts, ctx->nbr_mask, stride, ctx->overflow, n_overflow,
+                 n));
   MAFP_TIMED(ctx, s, "k_nbr<T,false>(overflow cells)",
              k_nbr<T, false><<<nbr_blocks, kNbrThreads, kNbrSmemBytes, s>>>(
       cg, ctx->ucell, ctx->overflow, n_overflow, spos, vin, ctx->cell_start,
