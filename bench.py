@@ -85,7 +85,7 @@ def parse():
                          "tray: the 16M-particle 20-step loop with model transitions")
     ap.add_argument("--tuning", default=None,
                     help="fixed launch shapes 'g3d,g2d,gapply[,ggrad3d[,ggrad2d]]' instead of the "
-                         "autotuner (the adjoint's default 4 and 2)")
+                         "autotuner (the adjoint's default 2 and 2)")
     return ap.parse_args()
 
 
@@ -294,7 +294,7 @@ def bench_gpu(args):
     if args.tuning:
         g = [int(v) for v in args.tuning.split(",")]
         ctx.set_tuning(stencil3d_group=g[0], stencil2d_group=g[1], apply_group=g[2],
-                       grad3d_group=g[3] if len(g) > 3 else 4,
+                       grad3d_group=g[3] if len(g) > 3 else 2,
                        grad2d_group=g[4] if len(g) > 4 else 2)
         tuned = {"tuning": ctx.tuning(), "source": "command line"}
     else:

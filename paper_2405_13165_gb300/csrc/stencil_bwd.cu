@@ -79,22 +79,28 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
   // per-operator output scale of the forward kernel: gradient 1/h, Laplacian 1/h^2
   const C h2inv = hinv * hinv;
   const V fi = ld4(fields + i);
-  V go[4];
+  // gout of row i; 3D rows fold the output scale into it (gs = gout * (1/h, 1/h,
+  // 1/h, 1/h^2) per field), film rows keep it unscaled for the frame terms
+  C gs[4][4];
 #pragma unroll
-  for (int f = 0; f < 4; ++f) go[f] = ld4(gout + 4 * i + f);
-  // gbar (scaled) of one neighbour, in the basis' operator order
+  for (int f = 0; f < 4; ++f) {
+    const V g = ld4(gout + 4 * i + f);
+    const C sg = M == 10 ? hinv : C(1), sl = M == 10 ? h2inv : C(1);
+    gs[f][0] = C(g.x) * sg; gs[f][1] = C(g.y) * sg; gs[f][2] = C(g.z) * sg; gs[f][3] = C(g.w) * sl;
+  }
+  // gbar (scaled) of one neighbour, in the basis' operator order; g4 = the
+  // unscaled sum_f gout[i][f][.] du_f of film rows
   auto gbar = [&](const V &fj, C (&gb)[NR], C (&g4)[4]) {
     const C du[4] = {C(fj.x) - C(fi.x), C(fj.y) - C(fi.y), C(fj.z) - C(fi.z), C(fj.w) - C(fi.w)};
-    g4[0] = g4[1] = g4[2] = g4[3] = C(0);
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      g4[0] += C(go[f].x) * du[f];
-      g4[1] += C(go[f].y) * du[f];
-      g4[2] += C(go[f].z) * du[f];
-      g4[3] += C(go[f].w) * du[f];
+    for (int c = 0; c < 4; ++c) {
+      C v = gs[0][c] * du[0];
+#pragma unroll
+      for (int f = 1; f < 4; ++f) v = fma(gs[f][c], du[f], v);
+      g4[c] = v;
     }
     if constexpr (M == 10) {
-      gb[0] = g4[0] * hinv; gb[1] = g4[1] * hinv; gb[2] = g4[2] * hinv; gb[3] = g4[3] * h2inv;
+      gb[0] = g4[0]; gb[1] = g4[1]; gb[2] = g4[2]; gb[3] = g4[3];
     } else {
       gb[0] = (g4[0] * t1[0] + g4[1] * t1[1] + g4[2] * t1[2]) * hinv;
       gb[1] = (g4[0] * t2[0] + g4[1] * t2[1] + g4[2] * t2[2]) * hinv;
@@ -144,19 +150,17 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
   }
 #pragma unroll
   for (int r = 0; r < M; ++r) {
-    C g4[4] = {0, 0, 0, 0};
+    C g4[4];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      g4[0] += C(go[f].x) * Bf[f * M + r];
-      g4[1] += C(go[f].y) * Bf[f * M + r];
-      g4[2] += C(go[f].z) * Bf[f * M + r];
-      g4[3] += C(go[f].w) * Bf[f * M + r];
+    for (int c = 0; c < 4; ++c) {
+      C v = gs[0][c] * Bf[r];
+#pragma unroll
+      for (int f = 1; f < 4; ++f) v = fma(gs[f][c], Bf[f * M + r], v);
+      g4[c] = v;
     }
     if constexpr (M == 10) {
-      R[0 * M + r] = g4[0] * hinv;
-      R[1 * M + r] = g4[1] * hinv;
-      R[2 * M + r] = g4[2] * hinv;
-      R[3 * M + r] = g4[3] * h2inv;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) R[c * M + r] = g4[c];
     } else {
       R[0 * M + r] = (g4[0] * t1[0] + g4[1] * t1[1] + g4[2] * t1[2]) * hinv;
       R[1 * M + r] = (g4[0] * t2[0] + g4[1] * t2[1] + g4[2] * t2[2]) * hinv;
@@ -219,40 +223,45 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
   auto pass2 = [&](const V &xj, const V &fj, int j, bool ok) {
     if (!ok || j == i) return;
     C p[M], gb[NR], g4[4];
-    const C w = basis_at<M, C>(xi, xj, hinv, t1, t2, sp, p);
-    gbar(fj, gb, g4);
     const C dx = C(xj.x) - C(xi.x), dy = C(xj.y) - C(xi.y), dz = C(xj.z) - C(xi.z);
+    // one exponential serves W and W' (W'(s)/s = a2 exp(-alpha s^2))
+    C ew;
+    const C w = basis_at<M, C>(xi, xj, hinv, t1, t2, sp, p, &ew);
     const C s2 = ((dx * dx + dy * dy) + dz * dz) * (hinv * hinv);
-    const C dws = s2 <= C(1) ? a2 * exp(-sp.alpha * s2) : C(0);
+    const C dws = s2 <= C(1) ? a2 * ew : C(0);
+    gbar(fj, gb, g4);
     // pbar = w sum_k ((gbar_k - t_k) lambda_k - s_k mu_k); pbar_0 is not needed
-    // (d p_0 / d q = 0) and the factor w is applied to the gradient below
+    // (d p_0 / d q = 0) and the factor w is applied to the gradient below.
+    // Every sum is a chain of fused multiply-adds (p_0 = 1 starts the dot products).
     C wbar = 0, pbar[M], s01[2] = {0, 0};
 #pragma unroll
-    for (int r = 0; r < M; ++r) pbar[r] = 0;
-#pragma unroll
     for (int k = 0; k < NR; ++k) {
-      C s = 0, t = 0;
+      C s = lam[k][0], t = mu[k][0];
 #pragma unroll
-      for (int r = 0; r < M; ++r) {
-        s += p[r] * lam[k][r];
-        t += p[r] * mu[k][r];
+      for (int r = 1; r < M; ++r) {
+        s = fma(p[r], lam[k][r], s);
+        t = fma(p[r], mu[k][r], t);
       }
       if (k < 2) s01[k] = s;
       const C a = gb[k] - t;
-      wbar += a * s;
+      wbar = fma(a, s, wbar);
 #pragma unroll
-      for (int r = 1; r < M; ++r) pbar[r] += a * lam[k][r] - s * mu[k][r];
+      for (int r = 1; r < M; ++r) {
+        pbar[r] = k == 0 ? a * lam[k][r] : fma(a, lam[k][r], pbar[r]);
+        pbar[r] = fma(-s, mu[k][r], pbar[r]);
+      }
     }
     const C wq = dws * wbar;
     C d[3];
     if constexpr (M == 10) {
       const C qx = dx * hinv, qy = dy * hinv, qz = dz * hinv;
-      const C gx = w * (pbar[1] + C(2) * qx * pbar[4] + qy * pbar[7] + qz * pbar[8]);
-      const C gy = w * (pbar[2] + C(2) * qy * pbar[5] + qx * pbar[7] + qz * pbar[9]);
-      const C gz = w * (pbar[3] + C(2) * qz * pbar[6] + qx * pbar[8] + qy * pbar[9]);
-      d[0] = (gx + wq * qx) * hinv;
-      d[1] = (gy + wq * qy) * hinv;
-      d[2] = (gz + wq * qz) * hinv;
+      const C wh = w * hinv, wqh = wq * hinv;
+      const C gx = fma(C(2) * qx, pbar[4], fma(qy, pbar[7], fma(qz, pbar[8], pbar[1])));
+      const C gy = fma(C(2) * qy, pbar[5], fma(qx, pbar[7], fma(qz, pbar[9], pbar[2])));
+      const C gz = fma(C(2) * qz, pbar[6], fma(qx, pbar[8], fma(qy, pbar[9], pbar[3])));
+      d[0] = fma(wqh, qx, wh * gx);
+      d[1] = fma(wqh, qy, wh * gy);
+      d[2] = fma(wqh, qz, wh * gz);
     } else {
       const C xi_ = p[1], et_ = p[2];
       const C xb = w * (pbar[1] + C(2) * xi_ * pbar[3] + et_ * pbar[4]);

@@ -124,12 +124,21 @@ __device__ __forceinline__ C weight_w(C s2, const StParams<C> &sp) {
 }
 
 // Monomial basis at one neighbour; returns w (0 for j outside the unit support).
+// With e_out, also exp(-alpha s^2) (for W'), from the same exponential as w.
 template <int M, typename C, typename V>
 __device__ __forceinline__ C basis_at(const V &xi, const V &xj, C hinv, const C (&t1)[3],
-                                      const C (&t2)[3], const StParams<C> &sp, C (&p)[M]) {
+                                      const C (&t2)[3], const StParams<C> &sp, C (&p)[M],
+                                      C *e_out = nullptr) {
   const C dx = C(xj.x) - C(xi.x), dy = C(xj.y) - C(xi.y), dz = C(xj.z) - C(xi.z);
   const C s2 = ((dx * dx + dy * dy) + dz * dz) * (hinv * hinv);
-  const C w = weight_w<C>(s2, sp);
+  C w;
+  if (e_out) {
+    const C e = exp(-sp.alpha * s2);
+    *e_out = e;
+    w = s2 <= C(1) ? (e - sp.ea) * sp.inv_den : C(0);
+  } else {
+    w = weight_w<C>(s2, sp);
+  }
   if constexpr (M == 10) {
     const C qx = dx * hinv, qy = dy * hinv, qz = dz * hinv;
     p[0] = C(1); p[1] = qx; p[2] = qy; p[3] = qz;
