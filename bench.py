@@ -33,7 +33,10 @@ sys.path.insert(0, ROOT)
 METRIC = ("particles/s for neighbour+PCA+stencil build, apply_ops GB/s; "
           "FP32-refined vs FP64 at 1e-4")
 UNIT = "particles/s"
-WORKLOAD = "jet-impingement cloud, 1M particles (cylinder r=0.05 m h=0.5 m + film disc r=1 m)"
+def workload_label(n: int) -> str:
+    size = "1M" if n == 1_000_000 else f"{n:,}"
+    return (f"jet-impingement cloud, {size} particles (cylinder r=0.05 m h=0.5 m + film disc "
+            f"r=1 m)")
 
 # Algorithmic work per unit (see the design notes): bytes of the gather-SpMV,
 # flops of the stencil build per same-model neighbour and per particle.
@@ -183,6 +186,39 @@ def error_per_output(a, b):
     p99 = np.percentile(comp, 99, axis=0)
     return {c: {"normwise": float(f"{nw[k]:.3e}"), "p99": float(f"{p99[k]:.3e}")}
             for k, c in enumerate(COLUMNS)}
+
+
+def analytic_consistency(cloud, out):
+    """Consistency of the applied operators with the analytic derivatives of
+    the sinusoid fields (a discretisation-error figure, not a parity check):
+    3D rows against the gradient and Laplacian, film rows (flat plate, normal
+    +z) against the in-plane gradient and the in-plane Laplacian.  Per output:
+    normwise max |a - e| / max |e| and the median of |a - e| / max(|e|, 1e-3 max|e|)."""
+    if not cloud.field_modes:
+        return None
+    x = cloud.pos_h[:, :3].astype(np.float64)
+    film = cloud.model == 1
+    e = np.zeros((cloud.n, 4, 4))
+    for f, kx, ky, kz, phi in cloud.field_modes:
+        arg = x @ np.array([kx, ky, kz]) + phi
+        c, sn = np.cos(arg), np.sin(arg)
+        e[:, f, 0] += kx * c
+        e[:, f, 1] += ky * c
+        e[:, f, 2] += np.where(film, 0.0, kz * c)
+        e[:, f, 3] -= np.where(film, kx * kx + ky * ky, kx * kx + ky * ky + kz * kz) * sn
+    a = np.asarray(out, np.float64).reshape(-1, 16)
+    e = e.reshape(-1, 16)
+    scale = np.abs(e).max(0)
+    diff = np.abs(a - e)
+    nw = diff.max(0) / np.where(scale > 0, scale, 1.0)
+    med = np.median(diff / np.maximum(np.abs(e), 1e-3 * scale), axis=0)
+    return {"per_output": {c: {"normwise": float(f"{nw[k]:.3e}"), "median": float(f"{med[k]:.3e}")}
+                           for k, c in enumerate(COLUMNS)},
+            "max_normwise": float(f"{nw.max():.3e}"),
+            "what": "FP32-refined outputs vs the analytic derivatives of the sinusoid fields "
+                    "(3D rows: gradient and Laplacian; film rows: in-plane gradient and "
+                    "Laplacian); discretisation error of the order-2 stencils at h = 3.5 dx, "
+                    "largest on one-sided boundary rows"}
 
 
 def gen_cloud(n):
@@ -417,6 +453,7 @@ def bench_gpu(args):
         kernels["nbr_mask"] = {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": fp32_peak,
                                "unit": "TFLOP/s", "ms": ms, "algorithmic": fl,
                                "candidate_tests": n_cand,
+                               "candidates_per_entry": round(n_cand / max(nnz, 1), 3),
                                "peak_src": "FP32 FMA issue rate at sampled clock"}
     ms, _ = kernel_ms("k_stencil_grad<f32,M=10")
     if ms:
@@ -487,7 +524,8 @@ def bench_gpu(args):
         t32 /= k64
         pipe.apply(d)
         out32 = pipe.out[:n].cpu().numpy()
-        fp64 = {"build_ms_fp64": round(t64, 3), "build_ms_fp32_refined": round(t32, 3),
+        fp64 = {"analytic": analytic_consistency(cloud, out32),
+                "build_ms_fp64": round(t64, 3), "build_ms_fp32_refined": round(t32, 3),
                 "repeats": k64, "speedup": round(t64 / t32, 2),
                 "build_particles_per_s_fp32_refined": round(n / (t32 * 1e-3), 1),
                 "build_particles_per_s_fp64": round(n / (t64 * 1e-3), 1)}
@@ -570,6 +608,14 @@ def bench_gpu(args):
         dt, thr, desc, m, o_out = cpu_oracle_sample(cloud, args.cpu_sample)
         cpu = {"value": round(m / dt, 1), "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": desc, "seconds": round(dt, 2)}
+        # the same oracle on one thread, for context, on the cloud's first 20k particles
+        import oracle
+        oracle.set_threads(1)
+        dt1, _, _, m1, _ = cpu_oracle_sample(cloud, 20_000)
+        oracle.set_threads(thr)
+        cpu["one_thread"] = {"value": round(m1 / dt1, 1), "unit": UNIT, "seconds": round(dt1, 2),
+                             "sample": f"first {m1} particles (cell order), the same stages, "
+                                       f"1 thread"}
         if fp64 is not None and m == n:
             # error per output of both GPU paths against the FP64 oracle on the whole cloud
             e32, e64 = error_per_output(out32, o_out), error_per_output(out64, o_out)
@@ -593,7 +639,7 @@ def bench_gpu(args):
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded jet-on-plate cloud)",
-            "config": {"workload": WORKLOAD, "n_particles": n, "nnz": nnz, "n_3d": n3, "n_2d": n2,
+            "config": {"workload": workload_label(args.n), "n_particles": n, "nnz": nnz, "n_3d": n3, "n_2d": n2,
                        "dx": round(cloud.dx, 7), "precision": "FP32 refined, FP64 retakes",
                        "step": "neighbours, detection, remap, stencils, apply, apply transpose"
                                + (", stencil adjoint" if have_bwd else ""),
@@ -900,10 +946,10 @@ def bench_reference(args):
         return
     cloud = gen_cloud(args.n)
     m = args.cpu_sample
-    for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
-        pass  # the oracle has no state to warm beyond loading its library
     import oracle
     oracle.build()
+    for _ in range(args.warmup):
+        cpu_oracle_sample(cloud, m)   # untimed
     times = []
     for _ in range(args.steps):
         dt, thr, desc, mm, _ = cpu_oracle_sample(cloud, m)
@@ -914,7 +960,8 @@ def bench_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms, 2), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded jet-on-plate cloud)",
-            "config": {"workload": WORKLOAD, "n_particles": cloud.n, "sample_particles": mm},
+            "config": {"workload": workload_label(args.n), "n_particles": cloud.n,
+                       "sample_particles": mm},
             "timed_region_s": round(sum(times), 2),
             "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "kind": "oracle",
                              "cores": thr, "sample": desc},

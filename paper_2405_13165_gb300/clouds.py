@@ -59,6 +59,8 @@ class Cloud:
     last: np.ndarray     # uint8  [N]     1 if transitioned in previous step
     dx: float = 0.0
     name: str = ""
+    # the modes of the sinusoid fields: (field, kappa_x, kappa_y, kappa_z, phi) each
+    field_modes: tuple = ()
 
     @property
     def n(self) -> int:
@@ -91,6 +93,8 @@ def concat(clouds: list[Cloud], name: str = "") -> Cloud:
         vals = [getattr(c, f.name) for c in clouds]
         if isinstance(vals[0], np.ndarray):
             kw[f.name] = np.ascontiguousarray(np.concatenate(vals, axis=0))
+        elif f.name == "field_modes":
+            kw[f.name] = vals[0] if all(v == vals[0] for v in vals) else ()
         else:
             kw[f.name] = vals[0]
     kw["name"] = name
@@ -98,11 +102,13 @@ def concat(clouds: list[Cloud], name: str = "") -> Cloud:
 
 
 def sinusoid_fields(xyz: np.ndarray, rng: np.random.Generator, modes: int = 4,
-                    kmin: float = 1.0, kmax: float = 8.0) -> np.ndarray:
+                    kmin: float = 1.0, kmax: float = 8.0, modes_out: list | None = None
+                    ) -> np.ndarray:
     """u, v, w, p = sum of `modes` sinusoids sin(kappa . x + phi).
 
     kappa has a direction uniform on the sphere and |kappa| ~ U[kmin, kmax]
-    (rad/m); phi ~ U[0, 2 pi).  Returns float32 [N,4].
+    (rad/m); phi ~ U[0, 2 pi).  Returns float32 [N,4]; with `modes_out`, also
+    appends (field, kappa_x, kappa_y, kappa_z, phi) of every mode to it.
     """
     out = np.zeros((xyz.shape[0], 4), dtype=np.float64)
     for f in range(4):
@@ -112,6 +118,8 @@ def sinusoid_fields(xyz: np.ndarray, rng: np.random.Generator, modes: int = 4,
             k = d * rng.uniform(kmin, kmax)
             phi = rng.uniform(0.0, 2.0 * math.pi)
             out[:, f] += np.sin(xyz @ k + phi)
+            if modes_out is not None:
+                modes_out.append((f, float(k[0]), float(k[1]), float(k[2]), float(phi)))
     return out.astype(np.float32)
 
 
@@ -128,11 +136,13 @@ def _finish(xyz: np.ndarray, model: np.ndarray, ptype: np.ndarray, normal: np.nd
     mass = (RHO_WATER * vol).astype(np.float32)
     diam = np.cbrt(6.0 * vol / math.pi).astype(np.float32)
     hfilm = np.where(model == MODEL_2D, film_h, 0.0).astype(np.float32)
-    vp = sinusoid_fields(pos_h[:, :3].astype(np.float64), rng)
+    modes: list = []
+    vp = sinusoid_fields(pos_h[:, :3].astype(np.float64), rng, modes_out=modes)
     return Cloud(pos_h=pos_h, model=model.astype(np.uint8), ptype=ptype.astype(np.uint8),
                  normal=normal.astype(np.float32), vp=vp, rho=rho, eta=eta, mass=mass,
                  diam=diam, hfilm=hfilm, h3d=np.full(n, h, dtype=np.float32),
-                 user=np.zeros(n, np.uint8), last=np.zeros(n, np.uint8), dx=dx, name=name)
+                 user=np.zeros(n, np.uint8), last=np.zeros(n, np.uint8), dx=dx, name=name,
+                 field_modes=tuple(modes))
 
 
 def _jitter(xyz: np.ndarray, planar: np.ndarray, dx: float, rng: np.random.Generator) -> np.ndarray:
