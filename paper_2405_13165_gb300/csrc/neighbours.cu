@@ -778,12 +778,19 @@ __global__ void __launch_bounds__(kFillThreads) k_nbr_fill(
         for (int w = w0; w < w1; ++w)
           mw[wp][w - w0][lane] = lane < np ? mask[(int64_t)w * stride + s0 + q] : 0u;
         __syncwarp();
+        // this lane's candidate of every word of the window, in registers (the
+        // window loop is unrolled; words past w1 are empty)
+        int32_t cvr[kFillWinWords];
+#pragma unroll
+        for (int ww = 0; ww < kFillWinWords; ++ww)
+          cvr[ww] = w0 + ww < w1 ? cv[ww * 32 + lane] : 0;
         for (int k = 0; k < np; ++k) {
           int32_t *crow = col + __shfl_sync(0xffffffffu, rs, k);
           int a = __shfl_sync(0xffffffffu, at, k);
-          for (int w = w0; w < w1; ++w) {
-            const uint32_t word = mw[wp][w - w0][k];
-            if ((word >> lane) & 1u) crow[a + __popc(word & lt)] = cv[(w - w0) * 32 + lane];
+#pragma unroll
+          for (int ww = 0; ww < kFillWinWords; ++ww) {
+            const uint32_t word = w0 + ww < w1 ? mw[wp][ww][k] : 0u;
+            if ((word >> lane) & 1u) crow[a + __popc(word & lt)] = cvr[ww];
             a += __popc(word);
           }
           if (lane == k) at = a;

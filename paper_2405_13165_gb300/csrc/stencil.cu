@@ -147,12 +147,13 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
       const C w = c4.w;
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
-        C s = 0;
+        C s = lam[k][0];   // p_0 = 1
 #pragma unroll
-        for (int r = 0; r < M; ++r) s += p[r] * lam[k][r];
+        for (int r = 1; r < M; ++r) s = fma(p[r], lam[k][r], s);
         const C c = w * s;
+        R[k * M] += c;
 #pragma unroll
-        for (int r = 0; r < M; ++r) R[k * M + r] += c * p[r];
+        for (int r = 1; r < M; ++r) R[k * M + r] = fma(c, p[r], R[k * M + r]);
       }
     }
     for (long long e0 = b + lane + (long long)ncache * G; e0 < e1; e0 += kGatherR * G) {
@@ -166,12 +167,13 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
         w = oks[u] ? w : C(0);
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-          C s = 0;
+          C s = lam[k][0];   // p_0 = 1
 #pragma unroll
-          for (int r = 0; r < M; ++r) s += p[r] * lam[k][r];
+          for (int r = 1; r < M; ++r) s = fma(p[r], lam[k][r], s);
           const C c = w * s;
+          R[k * M] += c;
 #pragma unroll
-          for (int r = 0; r < M; ++r) R[k * M + r] += c * p[r];
+          for (int r = 1; r < M; ++r) R[k * M + r] = fma(c, p[r], R[k * M + r]);
         }
       }
     }
@@ -195,32 +197,34 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
   }
   // ---- coefficients
   const C h2inv = hinv * hinv;
-  auto write_coef = [&](long long e, const C (&p)[M], C w) {
-    C c[NR];
+  // the output record of one entry: w p.lambda_k (+ w p.lamlo for the
+  // Laplacian) with the operator's scale 1/h or 1/h^2 folded into w
+  auto coef_of = [&](const C (&p)[M], C w) -> vec4_t<TS> {
+    const C wg = w * hinv, wl = w * h2inv;
+    C s[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
-      C s = 0;
+      C v = lam[k][0];   // p_0 = 1
 #pragma unroll
-      for (int r = 0; r < M; ++r) s += p[r] * lam[k][r];
+      for (int r = 1; r < M; ++r) v = fma(p[r], lam[k][r], v);
       if (REFINE && k == KL) {
-        C sl = 0;
+        C sl = lamlo[0];
 #pragma unroll
-        for (int r = 0; r < M; ++r) sl += p[r] * lamlo[r];
-        s += sl;
+        for (int r = 1; r < M; ++r) sl = fma(p[r], lamlo[r], sl);
+        v += sl;
       }
-      c[k] = w * s;
+      s[k] = v;
     }
-    vec4_t<TS> out;
     if constexpr (M == 10) {
-      out = mk4<TS>(TS(c[0] * hinv), TS(c[1] * hinv), TS(c[2] * hinv), TS(c[3] * h2inv));
+      return mk4<TS>(TS(wg * s[0]), TS(wg * s[1]), TS(wg * s[2]), TS(wl * s[3]));
     } else {
-      const C gx = (c[0] * t1[0] + c[1] * t2[0]) * hinv;
-      const C gy = (c[0] * t1[1] + c[1] * t2[1]) * hinv;
-      const C gz = (c[0] * t1[2] + c[1] * t2[2]) * hinv;
-      out = mk4<TS>(TS(gx), TS(gy), TS(gz), TS(c[2] * h2inv));
+      const C gx = wg * fma(s[0], t1[0], s[1] * t2[0]);
+      const C gy = wg * fma(s[0], t1[1], s[1] * t2[1]);
+      const C gz = wg * fma(s[0], t1[2], s[1] * t2[2]);
+      return mk4<TS>(TS(gx), TS(gy), TS(gz), TS(wl * s[2]));
     }
-    st4(coef + e, out);
   };
+  auto write_coef = [&](long long e, const C (&p)[M], C w) { st4(coef + e, coef_of(p, w)); };
   for (int q = 0; q < ncache; ++q) {
     const float4 c4 = qw[q * G + lane];
     C p[M];
@@ -240,28 +244,7 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
     if (oks[u]) {
       C p[M];
       const C w = basis_at<M, C>(xi, xs[u], hinv, t1, t2, sp, p);
-      C c[NR];
-#pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        C s = 0;
-#pragma unroll
-        for (int r = 0; r < M; ++r) s += p[r] * lam[k][r];
-        if (REFINE && k == KL) {
-          C sl = 0;
-#pragma unroll
-          for (int r = 0; r < M; ++r) sl += p[r] * lamlo[r];
-          s += sl;
-        }
-        c[k] = w * s;
-      }
-      if constexpr (M == 10) {
-        out = mk4<TS>(TS(c[0] * hinv), TS(c[1] * hinv), TS(c[2] * hinv), TS(c[3] * h2inv));
-      } else {
-        const C gx = (c[0] * t1[0] + c[1] * t2[0]) * hinv;
-        const C gy = (c[0] * t1[1] + c[1] * t2[1]) * hinv;
-        const C gz = (c[0] * t1[2] + c[1] * t2[2]) * hinv;
-        out = mk4<TS>(TS(gx), TS(gy), TS(gz), TS(c[2] * h2inv));
-      }
+      out = coef_of(p, w);
     }
     st4(coef + e, out);
     }
