@@ -116,14 +116,27 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
   // entries of this lane, and how many of them the cache holds
   const int nloc = e1 > b + lane ? (int)((e1 - b - lane + G - 1) / G) : 0;
   const int ncache = KC > 0 ? min(nloc, KC) : 0;
-  // ---- solve
+  // ---- solve: lane k of the group solves right-hand side k (a warp issues one
+  // solve for all of its groups' lanes at once instead of NR in a row; lanes
+  // k >= NR repeat one) and the group reads the solutions back from shared memory
+  static_assert(G >= NR, "one lane per right-hand side");
+  const int kq = lane % NR;
   C lam[NR][M];
+  {
+    C bb[M], x[M];
 #pragma unroll
-  for (int k = 0; k < NR; ++k) {
-    C bb[M];
+    for (int r = 0; r < M; ++r) bb[r] = rhs<M, C>(kq, r);
+    chol_solve_s<M, C>(Ls, invd, bb, x);
+    if (lane < NR) {
 #pragma unroll
-    for (int r = 0; r < M; ++r) bb[r] = rhs<M, C>(k, r);
-    chol_solve_s<M, C>(Ls, invd, bb, lam[k]);
+      for (int r = 0; r < M; ++r) sm[lane * M + r] = x[r];
+    }
+    __syncwarp(gm);
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+#pragma unroll
+      for (int r = 0; r < M; ++r) lam[k][r] = sm[k * M + r];
+    __syncwarp(gm);
   }
   // The Laplacian's refinement correction is kept apart (lamlo) instead of
   // being added into lam: its solution has entries ~100x its coefficients on
@@ -181,17 +194,25 @@ __device__ void stencil_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t
 #pragma unroll
     for (int k = 0; k < VR / G; ++k) sm[lane * (VR / G) + k] = R[k];
     __syncwarp(gm);
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
+    {
+      // the corrections, one right-hand side per lane as above
       C rr[M], d[M];
 #pragma unroll
-      for (int r = 0; r < M; ++r) rr[r] = rhs<M, C>(k, r) - sm[k * M + r];
+      for (int r = 0; r < M; ++r) rr[r] = rhs<M, C>(kq, r) - sm[kq * M + r];
+      __syncwarp(gm);   // every lane has its residual before the corrections overwrite it
       chol_solve_s<M, C>(Ls, invd, rr, d);
+      if (lane < NR) {
 #pragma unroll
-      for (int r = 0; r < M; ++r) {
-        if (k == KL) lamlo[r] = d[r];
-        else lam[k][r] += d[r];
+        for (int r = 0; r < M; ++r) sm[lane * M + r] = d[r];
       }
+      __syncwarp(gm);
+#pragma unroll
+      for (int k = 0; k < NR; ++k)
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+          if (k == KL) lamlo[r] = sm[k * M + r];
+          else lam[k][r] += sm[k * M + r];
+        }
     }
     __syncwarp(gm);
   }
