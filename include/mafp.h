@@ -94,6 +94,7 @@ typedef struct {
                               percent of the cloud's largest h, 100..200 (larger cells:
                               more candidates per particle, fewer cells to stage); the
                               neighbour sets are the same for every value */
+  int32_t classify_group;  /* lanes per particle in mafp_classify_pca: 2, 4, 8 or 16 */
 } mafp_tuning;
 
 /* Device-side status block, copied out by mafp_get_status. */

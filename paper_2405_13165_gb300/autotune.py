@@ -1,6 +1,6 @@
 """Autotuner of the launch shapes: the neighbour search's cell tile (cell edge
-in percent of max h) and the lanes per particle / per row of build_stencils,
-apply_ops and the stencil adjoint.
+in percent of max h) and the lanes per particle / per row of classify_pca,
+build_stencils, apply_ops and the stencil adjoint.
 
 For a cloud already on the device it times every supported group size of a
 stage with CUDA events (a few repetitions, best taken), keeps the fastest,
@@ -20,7 +20,8 @@ from . import mafp as M
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
 CHOICES = {"stencil3d_group": (8, 16, 32), "stencil2d_group": (4, 8, 16),
            "apply_group": (4, 8, 16), "grad3d_group": (2, 4, 8, 16, 32),
-           "grad2d_group": (2, 4, 8, 16), "cell_edge_pct": (100, 115, 130)}
+           "grad2d_group": (2, 4, 8, 16), "cell_edge_pct": (100, 115, 130),
+           "classify_group": (2, 4, 8, 16)}
 
 
 def mix_key(d, pipe, n: int) -> str:
@@ -68,6 +69,14 @@ def tune(ctx: M.Context, pipe, d, use_cache: bool = True, verbose: bool = False)
     timings["cell_edge_pct"] = res
     ctx.set_tuning(**best)
     pipe.neighbours(d)
+    res = {}
+    for g in CHOICES["classify_group"]:
+        ctx.set_tuning(**{**best, "classify_group": g})
+        res[g] = _time(lambda: pipe.classify(d))
+    best["classify_group"] = min(res, key=res.get)
+    timings["classify_group"] = res
+    ctx.set_tuning(**best)
+    pipe.classify(d)
     for knob in ("stencil3d_group", "stencil2d_group"):
         res = {}
         for g in CHOICES[knob]:

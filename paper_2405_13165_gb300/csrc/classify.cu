@@ -11,7 +11,6 @@
 namespace mafp {
 
 constexpr int kClsThreads = 128;
-constexpr int kClsGroup = 8;
 
 // Thresholds prepared on the host so the FP32 path compares in FP32 only.
 struct ClsConst {
@@ -344,12 +343,15 @@ __global__ void __launch_bounds__(kClsThreads) k_smooth(int64_t n, const uint8_t
   }
 }
 
-int classify_pca(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h, const uint8_t *model,
-                 const uint8_t *type, const void *normal, const void *vol, const void *h3d,
-                 const uint8_t *user, const uint8_t *last, const int64_t *row_ptr,
-                 const int32_t *col, uint8_t *flag, uint8_t *preflag, void *eig, void *frame,
-                 void *hfilm, uint8_t *near, cudaStream_t s) {
-  constexpr int G = kClsGroup;
+template <int G>
+static int classify_pca_g(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h,
+                          const uint8_t *model, const uint8_t *type, const void *normal,
+                          const void *vol, const void *h3d, const uint8_t *user,
+                          const uint8_t *last, const int64_t *row_ptr, const int32_t *col,
+                          uint8_t *flag, uint8_t *preflag, void *eig, void *frame, void *hfilm,
+                          uint8_t *near, cudaStream_t s) {
+  static const KernelName n64("k_classify<double,G=%d>", G), n32("k_classify<float,G=%d>", G),
+      nsm("k_smooth<G=%d>", G);
   const int blocks = grid_for(n * G, kClsThreads, sm_count() * 32);
   ClsConst kc;
   kc.cth = cos(ctx->prm.theta_star);
@@ -360,23 +362,47 @@ int classify_pca(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h, con
   kc.hfilm_band_f = (float)ctx->prm.hfilm_band;
   const long long *rp = reinterpret_cast<const long long *>(row_ptr);
   if (dtype == MAFP_F64) {
-    MAFP_TIMED(ctx, s, "k_classify<double>",
+    MAFP_TIMED(ctx, s, n64.s,
                k_classify<double, G><<<blocks, kClsThreads, 0, s>>>(
                    n, (const double4_16a *)pos_h, model, type, (const double4_16a *)normal,
                    (const double *)vol, (const double *)h3d, user, rp, col, preflag,
                    (double4_16a *)eig, (double4_16a *)frame, (double *)hfilm, near, ctx->prm,
                    kc, ctx->d_status));
   } else {
-    MAFP_TIMED(ctx, s, "k_classify<float>",
+    MAFP_TIMED(ctx, s, n32.s,
                k_classify<float, G><<<blocks, kClsThreads, 0, s>>>(
                    n, (const float4 *)pos_h, model, type, (const float4 *)normal,
                    (const float *)vol, (const float *)h3d, user, rp, col, preflag, (float4 *)eig,
                    (float4 *)frame, (float *)hfilm, near, ctx->prm, kc, ctx->d_status));
   }
-  MAFP_TIMED(ctx, s, "k_smooth",
+  MAFP_TIMED(ctx, s, nsm.s,
              k_smooth<G><<<blocks, kClsThreads, 0, s>>>(n, model, preflag, last, rp, col, flag));
   MAFP_LAUNCH_CHECK(ctx);
   return MAFP_OK;
+}
+
+// Lanes per particle: the context's classify_group (the FP32 sums are reduced
+// over the group, so the eigenvalues differ only by rounding; every decision
+// near a threshold is retaken in FP64 whatever the group).
+int classify_pca(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h, const uint8_t *model,
+                 const uint8_t *type, const void *normal, const void *vol, const void *h3d,
+                 const uint8_t *user, const uint8_t *last, const int64_t *row_ptr,
+                 const int32_t *col, uint8_t *flag, uint8_t *preflag, void *eig, void *frame,
+                 void *hfilm, uint8_t *near, cudaStream_t s) {
+  switch (ctx->tune.classify_group) {
+    case 2:
+      return classify_pca_g<2>(ctx, n, dtype, pos_h, model, type, normal, vol, h3d, user, last,
+                               row_ptr, col, flag, preflag, eig, frame, hfilm, near, s);
+    case 4:
+      return classify_pca_g<4>(ctx, n, dtype, pos_h, model, type, normal, vol, h3d, user, last,
+                               row_ptr, col, flag, preflag, eig, frame, hfilm, near, s);
+    case 16:
+      return classify_pca_g<16>(ctx, n, dtype, pos_h, model, type, normal, vol, h3d, user, last,
+                                row_ptr, col, flag, preflag, eig, frame, hfilm, near, s);
+    default:
+      return classify_pca_g<8>(ctx, n, dtype, pos_h, model, type, normal, vol, h3d, user, last,
+                               row_ptr, col, flag, preflag, eig, frame, hfilm, near, s);
+  }
 }
 
 }  // namespace mafp

@@ -210,6 +210,7 @@ inline void default_tuning(mafp_tuning *t) {
   t->grad3d_group = 2;
   t->grad2d_group = 2;
   t->cell_edge_pct = 100;
+  t->classify_group = 2;
 }
 
 // Name of a kernel instance for the timing record: built once (function-local

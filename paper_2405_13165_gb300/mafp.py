@@ -49,7 +49,8 @@ class Status(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("stencil3d_group", C.c_int32), ("stencil2d_group", C.c_int32),
                 ("apply_group", C.c_int32), ("grad3d_group", C.c_int32),
-                ("grad2d_group", C.c_int32), ("cell_edge_pct", C.c_int32)]
+                ("grad2d_group", C.c_int32), ("cell_edge_pct", C.c_int32),
+                ("classify_group", C.c_int32)]
 
 
 class KernelTime(C.Structure):

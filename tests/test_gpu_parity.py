@@ -227,17 +227,21 @@ def test_apply_transpose(orc, dtype, scatter):
     assert np.all(np.abs(got - want).max(0) <= TOL[dtype] * scale)
 
 
-@pytest.mark.parametrize("g3,g2,ga", [(8, 4, 4), (16, 16, 16), (32, 8, 8)])
-def test_launch_shapes_agree_with_oracle(orc, g3, g2, ga):
+@pytest.mark.parametrize("g3,g2,ga,gc", [(8, 4, 4, 2), (16, 16, 16, 4), (32, 8, 8, 16)])
+def test_launch_shapes_agree_with_oracle(orc, g3, g2, ga, gc):
     c = C.config_small()
     o = _oracle_all(orc, c)
     ctx = M.Context(c.n)
-    ctx.set_tuning(stencil3d_group=g3, stencil2d_group=g2, apply_group=ga)
+    ctx.set_tuning(stencil3d_group=g3, stencil2d_group=g2, apply_group=ga, classify_group=gc)
     g, *_ = run_gpu(c, M.F32_REFINED, ctx=ctx)
+    _check_flags(g, o)
     err, _ = stencil_rowwise_error_vec(o["row_ptr"], g["coef"], o["coef"])
     assert np.all(err <= TOL[M.F32_REFINED]), err
     nw, p99 = column_error(g["out"], o["out"])
     assert np.all(nw <= TOL[M.F32_REFINED]), (nw, p99)
+    for bad in (1, 3, 32):
+        with pytest.raises(M.MafpError):
+            ctx.set_tuning(classify_group=bad)
 
 
 @pytest.mark.parametrize("pct", [100, 115, 130, 200])
