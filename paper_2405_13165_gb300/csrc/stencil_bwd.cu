@@ -264,17 +264,19 @@ __device__ int grad_particle(int64_t i, const vec4_t<TS> *pos, const uint8_t *mo
       d[2] = fma(wqh, qz, wh * gz);
     } else {
       const C xi_ = p[1], et_ = p[2];
-      const C xb = w * (pbar[1] + C(2) * xi_ * pbar[3] + et_ * pbar[4]);
-      const C eb = w * (pbar[2] + xi_ * pbar[4] + C(2) * et_ * pbar[5]);
-      d[0] = (xb * t1[0] + eb * t2[0]) * hinv + wq * dx * hinv * hinv;
-      d[1] = (xb * t1[1] + eb * t2[1]) * hinv + wq * dy * hinv * hinv;
-      d[2] = (xb * t1[2] + eb * t2[2]) * hinv + wq * dz * hinv * hinv;
+      // xbh, ebh = dL/dxi, dL/deta (with w) over h
+      const C wh = w * hinv, wqh2 = wq * h2inv;
+      const C xbh = wh * fma(C(2) * xi_, pbar[3], fma(et_, pbar[4], pbar[1]));
+      const C ebh = wh * fma(xi_, pbar[4], fma(C(2) * et_, pbar[5], pbar[2]));
+      d[0] = fma(xbh, t1[0], fma(ebh, t2[0], wqh2 * dx));
+      d[1] = fma(xbh, t1[1], fma(ebh, t2[1], wqh2 * dy));
+      d[2] = fma(xbh, t1[2], fma(ebh, t2[2], wqh2 * dz));
       // the frame through xi, eta and through c^xi t1 + c^eta t2 (c^xi = w s_0 / h);
       // only the normal components of dL/dt_k are needed
       const C dn = dx * nv[0] + dy * nv[1] + dz * nv[2];
       const C gn = g4[0] * nv[0] + g4[1] * nv[1] + g4[2] * nv[2];
-      tn1 += (xb * dn + w * s01[0] * gn) * hinv;
-      tn2 += (eb * dn + w * s01[1] * gn) * hinv;
+      tn1 = fma(xbh, dn, fma(wh * s01[0], gn, tn1));
+      tn2 = fma(ebh, dn, fma(wh * s01[1], gn, tn2));
       const C ze = dn * hinv;
       sc[0] += xi_; sc[1] += et_; sc[2] += ze;
       sq[0] += xi_ * xi_; sq[1] += et_ * et_; sq[2] += ze * ze;
