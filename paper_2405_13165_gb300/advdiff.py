@@ -11,7 +11,7 @@ x in [1, 2] and film elsewhere, buffer zone rebuilt every step.
            x_i += dt (uniform velocity); re-sort into cell order
 
 The temperature is the first field slot.  Library calls do the path; the
-driver's own updates (user criterion, Euler step, transport, permutation)
+loop's own updates (user criterion, Euler step, transport, permutation)
 are elementwise torch operations in a fixed order.
 """
 from __future__ import annotations

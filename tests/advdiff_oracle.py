@@ -1,5 +1,5 @@
 """The advection-diffusion loop on the CPU: every stage through the FP64
-oracle, the driver's own updates restated in numpy float32 (user criterion,
+oracle, the time loop's own updates restated in numpy float32 (user criterion,
 explicit Euler step, transport, cell-order permutation), and the analytic
 solution of the temperature problem."""
 import numpy as np

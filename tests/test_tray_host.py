@@ -1,4 +1,4 @@
-"""Host-side pieces of the tray loop: the torch driver's advection and user
+"""Host-side pieces of the tray loop: the torch loop's advection and user
 criterion agree bit for bit with the numpy restatement the oracle loop uses,
 and two oracle steps keep the loop's invariants (mass, plate contact)."""
 import numpy as np
