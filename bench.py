@@ -188,6 +188,26 @@ def error_per_output(a, b):
             for k, c in enumerate(COLUMNS)}
 
 
+def oracle_reorder_spread(cloud):
+    """How far the FP64 oracle's own outputs move when every row is summed in
+    the reverse order (stencils and apply): the rounding floor that any FP64
+    evaluation of the same rows shares, per output column (normwise)."""
+    import oracle
+    rp, col = oracle.neighbours(cloud.pos_h)
+    coef, _, _ = oracle.stencils(cloud.pos_h, cloud.model, rp, col)
+    out = oracle.apply(rp, col, coef, cloud.vp)
+    col_r = col.copy()
+    for i in range(cloud.n):
+        col_r[rp[i]:rp[i + 1]] = col[rp[i]:rp[i + 1]][::-1]
+    coef_r, _, _ = oracle.stencils(cloud.pos_h, cloud.model, rp, col_r)
+    out_r = oracle.apply(rp, col_r, coef_r, cloud.vp)
+    e = error_per_output(out_r, out)
+    return {"per_output": {k: v["normwise"] for k, v in e.items()},
+            "max_normwise": max(v["normwise"] for v in e.values()),
+            "what": "FP64 oracle with each row's summation order reversed vs the FP64 oracle "
+                    "(normwise per output): the FP64 rounding floor of these rows"}
+
+
 def analytic_consistency(cloud, out):
     """Consistency of the applied operators with the analytic derivatives of
     the sinusoid fields (a discretisation-error figure, not a parity check):
@@ -624,6 +644,7 @@ def bench_gpu(args):
                 "fp32_refined_max_normwise": max(v["normwise"] for v in e32.values()),
                 "fp32_refined_max_p99": max(v["p99"] for v in e32.values()),
                 "fp64_max_normwise": max(v["normwise"] for v in e64.values()),
+                "fp64_oracle_reorder_spread": oracle_reorder_spread(cloud),
                 "bar": {"fp32_refined": 1e-4, "fp64": 1e-10},
                 "measure": "per field.operator over all particles: normwise max|a-b|/max|b|, "
                            "p99 of |a-b|/max(|b|, 1e-3 max|b|); b = FP64 oracle"}

@@ -324,6 +324,9 @@ int mafp_build_stencils_backward(mafp_ctx *ctx, int64_t n, int32_t dtype, const 
  *   x_i + k (H/gamma) n_i, k = 1..gamma (the last free surface, others
  *   interior), data copied, mass m/(1+gamma) each; the particle becomes a 3D wall.
  *  Survivors keep their relative order; added particles follow, by (i, k).
+ *   row_ptr/col  the neighbourhoods S of Eq. Nbd from mafp_build_neighbours;
+ *            the candidates are found from the rows of the flagged particles,
+ *            which relies on S being symmetric (j in S_b exactly when b in S_j)
  *   in/out   mafp_state of device arrays (out capacity cap_out rows)
  *   old2new  int32 [n] written: new index or -1 when deleted
  *   n_out_dev int64 [1] written: particle count after the transition

@@ -2,7 +2,9 @@
 //  1. owner: every interior / free-surface 3D particle b that neighbours a
 //     particle flagged 3D -> 2D finds its nearest 3D wall particle j^w in S_b
 //     (squared distance in FP64, ties to the lower index); b is deleted and
-//     mapped onto j^w when j^w is flagged.  gamma of every 2D -> 3D particle.
+//     mapped onto j^w when j^w is flagged.  The candidates b are marked from
+//     the rows of the flagged particles (S is symmetric), so only they search.
+//     gamma of every 2D -> 3D particle.
 //  2. scans: survivor positions, appended-particle offsets, n_out.
 //  3. survivors copied; 3D -> 2D particles aggregate their set T_i;
 //     2D -> 3D particles split their mass and emit gamma new particles.
@@ -24,55 +26,90 @@ __device__ __forceinline__ int gamma_of(double H, double h3d, double c_psi) {
   return (int)ceil(__ddiv_rn(H, psi_t));
 }
 
+// Every particle: no owner yet, kept, and gamma of the 2D -> 3D particles.
 template <typename T>
-__global__ void k_owner(int64_t n, StateT<T> in, const uint8_t *flag, const long long *row_ptr,
-                        const int32_t *col, int32_t *owner, int32_t *keep, int32_t *gam,
-                        double c_psi) {
+__global__ void k_owner_seed(int64_t n, StateT<T> in, const uint8_t *flag, int32_t *owner,
+                             int32_t *keep, int32_t *gam, double c_psi) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n; b += stride) {
+    owner[b] = -1;
+    keep[b] = 1;
+    gam[b] = (flag[b] == 2 && in.model[b] == MAFP_MODEL_2D)
+                 ? gamma_of((double)in.hfilm[b], (double)in.h3d[b], c_psi)
+                 : 0;
+  }
+}
+
+// Candidates of Alg. 3: the interior / free-surface 3D particles b that have a
+// 3D particle j flagged 3D -> 2D in S_b.  S is symmetric (Eq. Nbd), so one
+// warp per flagged j marks the candidates in its own row (owner[b] = -2);
+// only they search for a wall below.
+__global__ void k_owner_mark(int64_t n, const uint8_t *model, const uint8_t *type,
+                             const uint8_t *flag, const long long *row_ptr, const int32_t *col,
+                             int32_t *owner) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t b = wid; b < n; b += nwarps) {
-    const uint8_t mb = in.model[b];
-    int32_t own = -1;
-    if (mb == MAFP_MODEL_3D && in.type[b] != MAFP_TYPE_WALL) {
-      const long long r0 = row_ptr[b], r1 = row_ptr[b + 1];
-      int cand = 0;
+  // the warp tests 32 particles at once and walks the rows of the flagged ones
+  for (int64_t j0 = wid * 32; j0 < n; j0 += nwarps * 32) {
+    const int64_t jl = j0 + lane;
+    unsigned m = __ballot_sync(0xffffffffu,
+                               jl < n && flag[jl] == 1 && model[jl] == MAFP_MODEL_3D);
+    while (m) {
+      const int64_t j = j0 + __ffs(m) - 1;
+      m &= m - 1;
+      const long long r0 = row_ptr[j], r1 = row_ptr[j + 1];
       for (long long e = r0 + lane; e < r1; e += 32) {
-        const int j = col[e];
-        if (in.model[j] == MAFP_MODEL_3D && flag[j] == 1) cand = 1;
-      }
-      if (__any_sync(0xffffffffu, cand)) {
-        const vec4_t<T> xb = ld4(in.pos_h + b);
-        double best = INFINITY;
-        int jw = INT_MAX;
-        for (long long e = r0 + lane; e < r1; e += 32) {
-          const int j = col[e];
-          if (in.model[j] != MAFP_MODEL_3D || in.type[j] != MAFP_TYPE_WALL) continue;
-          const vec4_t<T> xj = ld4(in.pos_h + j);
-          const double d2 = dist2_64(xb.x, xb.y, xb.z, xj.x, xj.y, xj.z);
-          if (d2 < best || (d2 == best && j < jw)) {
-            best = d2;
-            jw = j;
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-          const int oj = __shfl_xor_sync(0xffffffffu, jw, o);
-          if (ob < best || (ob == best && oj < jw)) {
-            best = ob;
-            jw = oj;
-          }
-        }
-        if (jw != INT_MAX && flag[jw] == 1) own = jw;
+        const int b = col[e];
+        if (model[b] == MAFP_MODEL_3D && type[b] != MAFP_TYPE_WALL) owner[b] = -2;
       }
     }
-    if (lane == 0) {
-      owner[b] = own;
-      keep[b] = own < 0 ? 1 : 0;
-      gam[b] = (flag[b] == 2 && mb == MAFP_MODEL_2D)
-                   ? gamma_of((double)in.hfilm[b], (double)in.h3d[b], c_psi)
-                   : 0;
+  }
+}
+
+// Every candidate b finds its nearest 3D wall particle j^w in S_b (FP64 squared
+// distance, ties to the lower index) and is mapped onto it when j^w is flagged.
+template <typename T>
+__global__ void k_owner(int64_t n, StateT<T> in, const uint8_t *flag, const long long *row_ptr,
+                        const int32_t *col, int32_t *owner, int32_t *keep) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // the warp tests 32 particles at once and searches for the marked ones
+  for (int64_t b0 = wid * 32; b0 < n; b0 += nwarps * 32) {
+    const int64_t bl = b0 + lane;
+    unsigned mk = __ballot_sync(0xffffffffu, bl < n && owner[bl] == -2);
+    while (mk) {
+      const int64_t b = b0 + __ffs(mk) - 1;
+      mk &= mk - 1;
+      const long long r0 = row_ptr[b], r1 = row_ptr[b + 1];
+      const vec4_t<T> xb = ld4(in.pos_h + b);
+      double best = INFINITY;
+      int jw = INT_MAX;
+      for (long long e = r0 + lane; e < r1; e += 32) {
+        const int j = col[e];
+        if (in.model[j] != MAFP_MODEL_3D || in.type[j] != MAFP_TYPE_WALL) continue;
+        const vec4_t<T> xj = ld4(in.pos_h + j);
+        const double d2 = dist2_64(xb.x, xb.y, xb.z, xj.x, xj.y, xj.z);
+        if (d2 < best || (d2 == best && j < jw)) {
+          best = d2;
+          jw = j;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, jw, o);
+        if (ob < best || (ob == best && oj < jw)) {
+          best = ob;
+          jw = oj;
+        }
+      }
+      const int32_t own = (jw != INT_MAX && flag[jw] == 1) ? jw : -1;
+      if (lane == 0) {
+        owner[b] = own;
+        keep[b] = own < 0 ? 1 : 0;
+      }
     }
   }
 }
@@ -142,47 +179,54 @@ __global__ void k_to2d(int64_t n, StateT<T> in, StateT<T> out, const uint8_t *fl
   const int lane = threadIdx.x & 31;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = wid; i < n; i += nwarps) {
-    if (!(flag[i] == 1 && in.model[i] == MAFP_MODEL_3D)) continue;
-    const vec4_t<T> xi = ld4(in.pos_h + i), ni = ld4(in.normal + i);
-    T s[7] = {0, 0, 0, 0, 0, 0, 0};  // vp(4), rho, eta, mass
-    T H = 0;
-    int cnt = 0;
-    for (long long e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
-      const int b = col[e];
-      if (owner[b] != (int32_t)i) continue;
-      const vec4_t<T> v = ld4(in.vp + b), xb = ld4(in.pos_h + b);
-      s[0] += v.x; s[1] += v.y; s[2] += v.z; s[3] += v.w;
-      s[4] += in.rho[b];
-      s[5] += in.eta[b];
-      s[6] += in.mass[b];
-      const T dn = fabs((xb.x - xi.x) * ni.x + (xb.y - xi.y) * ni.y + (xb.z - xi.z) * ni.z);
-      H = dn > H ? dn : H;
-      ++cnt;
-    }
+  // the warp tests 32 particles at once and maps the flagged ones
+  for (int64_t i0 = wid * 32; i0 < n; i0 += nwarps * 32) {
+    const int64_t il = i0 + lane;
+    unsigned fl = __ballot_sync(0xffffffffu,
+                                il < n && flag[il] == 1 && in.model[il] == MAFP_MODEL_3D);
+    while (fl) {
+      const int64_t i = i0 + __ffs(fl) - 1;
+      fl &= fl - 1;
+      const vec4_t<T> xi = ld4(in.pos_h + i), ni = ld4(in.normal + i);
+      T s[7] = {0, 0, 0, 0, 0, 0, 0};  // vp(4), rho, eta, mass
+      T H = 0;
+      int cnt = 0;
+      for (long long e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
+        const int b = col[e];
+        if (owner[b] != (int32_t)i) continue;
+        const vec4_t<T> v = ld4(in.vp + b), xb = ld4(in.pos_h + b);
+        s[0] += v.x; s[1] += v.y; s[2] += v.z; s[3] += v.w;
+        s[4] += in.rho[b];
+        s[5] += in.eta[b];
+        s[6] += in.mass[b];
+        const T dn = fabs((xb.x - xi.x) * ni.x + (xb.y - xi.y) * ni.y + (xb.z - xi.z) * ni.z);
+        H = dn > H ? dn : H;
+        ++cnt;
+      }
 #pragma unroll
-    for (int k = 0; k < 7; ++k) s[k] = group_sum<32>(s[k]);
-    cnt = group_sum<32>(cnt);
+      for (int k = 0; k < 7; ++k) s[k] = group_sum<32>(s[k]);
+      cnt = group_sum<32>(cnt);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T oh = __shfl_xor_sync(0xffffffffu, H, o);
-      H = oh > H ? oh : H;
-    }
-    if (lane == 0) {
-      const long long o = keep_scan[i];
-      const vec4_t<T> v = ld4(in.vp + i);
-      const T k = T(1) + T(cnt);
-      st4(out.vp + o, mk4<T>((v.x + s[0]) / k, (v.y + s[1]) / k, (v.z + s[2]) / k, (v.w + s[3]) / k));
-      const T rho = (in.rho[i] + s[4]) / k;
-      const T m = in.mass[i] + s[6];
-      out.rho[o] = rho;
-      out.eta[o] = (in.eta[i] + s[5]) / k;
-      out.mass[o] = m;
-      out.diam[o] = droplet_diameter<T>((double)m, (double)rho);
-      out.hfilm[o] = H;
-      out.model[o] = MAFP_MODEL_2D;
-      out.type[o] = MAFP_TYPE_WALL;
-      out.last[o] = 1;
+      for (int o = 16; o > 0; o >>= 1) {
+        const T oh = __shfl_xor_sync(0xffffffffu, H, o);
+        H = oh > H ? oh : H;
+      }
+      if (lane == 0) {
+        const long long o = keep_scan[i];
+        const vec4_t<T> v = ld4(in.vp + i);
+        const T k = T(1) + T(cnt);
+        st4(out.vp + o, mk4<T>((v.x + s[0]) / k, (v.y + s[1]) / k, (v.z + s[2]) / k, (v.w + s[3]) / k));
+        const T rho = (in.rho[i] + s[4]) / k;
+        const T m = in.mass[i] + s[6];
+        out.rho[o] = rho;
+        out.eta[o] = (in.eta[i] + s[5]) / k;
+        out.mass[o] = m;
+        out.diam[o] = droplet_diameter<T>((double)m, (double)rho);
+        out.hfilm[o] = H;
+        out.model[o] = MAFP_MODEL_2D;
+        out.type[o] = MAFP_TYPE_WALL;
+        out.last[o] = 1;
+      }
     }
   }
 }
@@ -235,9 +279,15 @@ static int remap_t(mafp_ctx *ctx, int64_t n, const mafp_state *in_, const uint8_
   long long *keep_scan = reinterpret_cast<long long *>(ctx->remap_i64);
   long long *gam_scan = keep_scan + (n + 1);
   const int sms = sm_count();
+  MAFP_TIMED(ctx, s, "k_owner_seed<T>",
+             k_owner_seed<T><<<grid_for(n, 256, sms * 16), 256, 0, s>>>(n, in, flag, owner, keep,
+                                                                    gam, ctx->prm.c_psi));
+  MAFP_TIMED(ctx, s, "k_owner_mark",
+             k_owner_mark<<<grid_for(n * 32, 256, sms * 32), 256, 0, s>>>(n, in.model, in.type, flag,
+                                                                       rp, col, owner));
   MAFP_TIMED(ctx, s, "k_owner<T>",
-             k_owner<T><<<grid_for(n * 32, 256, sms * 32), 256, 0, s>>>(n, in, flag, rp, col, owner, keep,
-                                                              gam, ctx->prm.c_psi));
+             k_owner<T><<<grid_for(n * 32, 256, sms * 32), 256, 0, s>>>(n, in, flag, rp, col, owner,
+                                                                     keep));
   MAFP_LAUNCH_CHECK(ctx);
   int rc = scan_i32_to_i64(ctx, keep, keep_scan, n, s);
   if (rc) return rc;
