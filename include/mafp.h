@@ -88,13 +88,13 @@ typedef struct {
   int32_t apply_group;     /* lanes per row in mafp_apply_ops / _backward: 4, 8 or 16 */
   int32_t grad3d_group;    /* lanes per 3D particle in mafp_build_stencils_backward: 2, 4,
                               8, 16 or 32 (the FP64 adjoint takes at least 8) */
-  int32_t grad2d_group;    /* lanes per 2D particle in mafp_build_stencils_backward: 2, 4,
-                              8 or 16 */
+  int32_t grad2d_group;    /* lanes per 2D particle in mafp_build_stencils_backward: 1, 2,
+                              4, 8 or 16 */
   int32_t cell_edge_pct;   /* cell tile of the neighbour search: the grid's cell edge in
                               percent of the cloud's largest h, 100..200 (larger cells:
                               more candidates per particle, fewer cells to stage); the
                               neighbour sets are the same for every value */
-  int32_t classify_group;  /* lanes per particle in mafp_classify_pca: 2, 4, 8 or 16 */
+  int32_t classify_group;  /* lanes per particle in mafp_classify_pca: 1, 2, 4, 8 or 16 */
 } mafp_tuning;
 
 /* Device-side status block, copied out by mafp_get_status. */

@@ -20,8 +20,8 @@ from . import mafp as M
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
 CHOICES = {"stencil3d_group": (8, 16, 32), "stencil2d_group": (4, 8, 16),
            "apply_group": (4, 8, 16), "grad3d_group": (2, 4, 8, 16, 32),
-           "grad2d_group": (2, 4, 8, 16), "cell_edge_pct": (100, 115, 130),
-           "classify_group": (2, 4, 8, 16)}
+           "grad2d_group": (1, 2, 4, 8, 16), "cell_edge_pct": (100, 115, 130),
+           "classify_group": (1, 2, 4, 8, 16)}
 
 
 def mix_key(d, pipe, n: int) -> str:

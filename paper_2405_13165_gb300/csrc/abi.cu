@@ -218,10 +218,12 @@ int mafp_set_tuning(mafp_ctx *ctx, const mafp_tuning *t) {
   if (!(ga == 4 || ga == 8 || ga == 16)) return fail(ctx, MAFP_EINVAL, "apply_group");
   if (!(gb == 2 || gb == 4 || gb == 8 || gb == 16 || gb == 32))
     return fail(ctx, MAFP_EINVAL, "grad3d_group");
-  if (!(gf == 2 || gf == 4 || gf == 8 || gf == 16)) return fail(ctx, MAFP_EINVAL, "grad2d_group");
+  if (!(gf == 1 || gf == 2 || gf == 4 || gf == 8 || gf == 16))
+    return fail(ctx, MAFP_EINVAL, "grad2d_group");
   if (t->cell_edge_pct < 100 || t->cell_edge_pct > 200) return fail(ctx, MAFP_EINVAL, "cell_edge_pct");
   const int gc = t->classify_group;
-  if (!(gc == 2 || gc == 4 || gc == 8 || gc == 16)) return fail(ctx, MAFP_EINVAL, "classify_group");
+  if (!(gc == 1 || gc == 2 || gc == 4 || gc == 8 || gc == 16))
+    return fail(ctx, MAFP_EINVAL, "classify_group");
   ctx->tune = *t;
   return MAFP_OK;
 }

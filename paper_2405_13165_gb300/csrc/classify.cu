@@ -390,6 +390,9 @@ int classify_pca(mafp_ctx *ctx, int64_t n, int32_t dtype, const void *pos_h, con
                  const int32_t *col, uint8_t *flag, uint8_t *preflag, void *eig, void *frame,
                  void *hfilm, uint8_t *near, cudaStream_t s) {
   switch (ctx->tune.classify_group) {
+    case 1:
+      return classify_pca_g<1>(ctx, n, dtype, pos_h, model, type, normal, vol, h3d, user, last,
+                               row_ptr, col, flag, preflag, eig, frame, hfilm, near, s);
     case 2:
       return classify_pca_g<2>(ctx, n, dtype, pos_h, model, type, normal, vol, h3d, user, last,
                                row_ptr, col, flag, preflag, eig, frame, hfilm, near, s);

@@ -446,6 +446,7 @@ static void launch_grad(mafp_ctx *ctx, cudaStream_t s, int64_t n, const void *po
     default: launch_grad_g<TS, C, 10, 32, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
   }
   switch (ctx->tune.grad2d_group) {
+    case 1: launch_grad_g<TS, C, 6, 1, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
     case 2: launch_grad_g<TS, C, 6, 2, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
     case 4: launch_grad_g<TS, C, 6, 4, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;
     case 16: launch_grad_g<TS, C, 6, 16, QUEUE>(ctx, s, n, pos_h, model, frame, rp, col, fields, gout, gpos, sp); break;

@@ -173,7 +173,7 @@ def test_adjoint_launch_shapes_agree_with_oracle(dtype):
     tol = 2e-3 if dtype != M.F64 else 1e-8
     gout = torch.tensor(Gr, dtype=d["pos_h"].dtype, device="cuda").contiguous()
     gpos = torch.empty_like(d["pos_h"])
-    for gb, gf in ((2, 2), (4, 2), (8, 4), (16, 8), (32, 16)):
+    for gb, gf in ((2, 1), (2, 2), (4, 2), (8, 4), (16, 8), (32, 16)):
         ctx.set_tuning(grad3d_group=gb, grad2d_group=gf)
         assert ctx.tuning()["grad3d_group"] == gb and ctx.tuning()["grad2d_group"] == gf
         gpos.fill_(float("nan"))
