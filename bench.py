@@ -33,10 +33,13 @@ sys.path.insert(0, ROOT)
 METRIC = ("particles/s for neighbour+PCA+stencil build, apply_ops GB/s; "
           "FP32-refined vs FP64 at 1e-4")
 UNIT = "particles/s"
+
+
 def workload_label(n: int) -> str:
     size = "1M" if n == 1_000_000 else f"{n:,}"
     return (f"jet-impingement cloud, {size} particles (cylinder r=0.05 m h=0.5 m + film disc "
             f"r=1 m)")
+
 
 # Algorithmic work per unit (see the design notes): bytes of the gather-SpMV,
 # flops of the stencil build per same-model neighbour and per particle.
