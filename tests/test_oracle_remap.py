@@ -139,3 +139,35 @@ def test_round_trip_2d_3d_2d(orc):
     assert abs(back["mass"].sum() - m0) <= 1e-12 * m0
     psi = 0.02 / gamma
     assert np.all(np.abs(back["hfilm"] - 0.02) <= psi + 1e-12)
+
+
+def test_candidates_from_flagged_rows_equal_the_definition(orc):
+    """Alg. 3's candidates (interior / free-surface 3D particles b with a 3D
+    particle flagged 3D -> 2D in S_b) are the same set when read from the rows
+    of the flagged particles, because S is symmetric (Eq. Nbd): the GPU remap
+    marks them that way.  Checked on the shallow cylinder (flagged floor) and
+    on a random cloud with variable h and an arbitrary flag set."""
+    clouds = [C.shallow_layer(dx=0.05, depth_layers=3, extent=1.0, cylinder=True, h_factor=6.0)]
+    rc = C.random_cloud(2000, seed=5, h_lo=0.05, h_hi=0.2)
+    clouds.append(rc)
+    for k, c in enumerate(clouds):
+        if k == 0:
+            rp, col, flag = _run(orc, c)
+        else:
+            rp, col = orc.neighbours(c.pos_h)
+            rng = np.random.default_rng(9)
+            flag = np.where(rng.random(c.n) < 0.05, 1, 0).astype(np.uint8)
+            c.model[:] = np.where(rng.random(c.n) < 0.8, 0, 1).astype(np.uint8)
+            c.ptype[:] = rng.integers(0, 3, c.n).astype(np.uint8)
+        is3 = c.model == 0
+        inner = is3 & (c.ptype != C.TYPE_WALL)
+        flagged = is3 & (flag == 1)
+        by_def = np.zeros(c.n, bool)
+        for b in np.nonzero(inner)[0]:
+            by_def[b] = flagged[col[rp[b]:rp[b + 1]]].any()
+        by_rows = np.zeros(c.n, bool)
+        for j in np.nonzero(flagged)[0]:
+            nb = col[rp[j]:rp[j + 1]]
+            by_rows[nb[inner[nb]]] = True
+        assert by_def.any()
+        np.testing.assert_array_equal(by_rows, by_def)
